@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the two-range pseudopotential lattice Boltzmann
+step (Fei et al., arXiv:1806.06943) on GB300.
+
+Workload (default, ``laplace_sweep_24``): the batched Laplace sweep, 24
+periodic lattices of sides 128..384 (droplet radii 10..45 at viscosity ratios
+1, 3 and 10, tau_c = 1), 1,520,640 sites, FP32 offset populations, all
+lattices advanced by one launch per kernel.  One benchmark step = one time
+step of the whole batch (density pass + fused force/collide/stream kernel).
+The L2 cache is flushed (256 MiB overwrite) before every timed step, outside
+the timed intervals; steps are timed on the device with CUDA events.
+
+Metric: two-species MLUPS = lattice sites x time steps / s / 1e6, where one
+site update advances both species.  With --gpus N (torchrun), every rank
+advances its own copy of the batch (weak scaling, no data-path collective);
+the value is the sum over ranks divided by the slowest rank's time.
+
+Side legs (skipped with --quick): the same batch in FP64, the 4096x4096
+dense emulsion in FP32 and FP64, an end-to-end job through the public API
+with host buffers, and the CPU oracle timed on a bounded sample.
+``--impl reference`` times the CPU oracle alone as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+C6 = dict(G_AB=3.0, G1=-7.4, G2=6.4)
+FLUSH_BYTES = 256 << 20
+BYTES_COLLIDE = {1: 152, 0: 304}   # algorithmic bytes / site: 18 pops read + 18 written + 2 rho read
+BYTES_DENSITY = {1: 80, 0: 160}    # 18 pops read + 2 rho written
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--quick", action="store_true", help="main leg only")
+    return ap.parse_args()
+
+
+# ---- distributed helpers (host logic, also used by the CPU tests) -----------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, local, world
+
+
+def init_dist(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---- workloads ----------------------------------------------------------------
+
+def sweep_fields():
+    from paper_1806_06943_gb300 import workloads as W
+    specs = W.laplace_sweep_specs()
+    fields = [W.droplet(s["nx"], s["ny"], s["R"], seed=W.BASE_SEED + 1 + i) for i, s in enumerate(specs)]
+    return specs, fields
+
+
+def make_batch(lb, specs, fields, precision, stream):
+    b = lb.Batch([dict(nx=s["nx"], ny=s["ny"], tau=s["tau"]) for s in specs], precision=precision,
+                 rho_ref=(1.0, 1.0), stream=stream, **C6)
+    for i, (s, r) in enumerate(zip(specs, fields)):
+        b.set_fields(i, r)
+        b.set_probe(i, s["nx"] / 2, s["ny"] / 2, s["R"])
+    return b
+
+
+# ---- clocks ----------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---- CPU oracle timing -------------------------------------------------------------
+
+def oracle_sample(target_s: float):
+    """The oracle advancing lattice 0 of the sweep (128x128, R=10, ratio 1)
+    for as many steps as fit in about target_s seconds; returns MLUPS."""
+    import oracle
+    specs, _ = None, None
+    from paper_1806_06943_gb300 import workloads as W
+    s0 = W.laplace_sweep_specs()[0]
+    rho = W.droplet(s0["nx"], s0["ny"], s0["R"], seed=W.BASE_SEED + 1)
+    sim = oracle.OracleSim(s0["nx"], s0["ny"], tau=s0["tau"], **C6)
+    sim.set_fields(rho)
+    t0 = time.perf_counter()
+    sim.step(20)
+    dt = time.perf_counter() - t0
+    n = max(20, int(target_s / max(dt, 1e-6) * 20))
+    t0 = time.perf_counter()
+    sim.step(n)
+    dt = time.perf_counter() - t0
+    sites = s0["nx"] * s0["ny"]
+    return sites * n / dt / 1e6, f"lattice 0 of the sweep ({s0['nx']}x{s0['ny']}, R={s0['R']:g}), {n} steps, {dt:.1f} s", n
+
+
+def run_reference(args):
+    rank, local, world = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1806_06943_gb300 import workloads as W
+    s0 = W.laplace_sweep_specs()[0]
+    rho = W.droplet(s0["nx"], s0["ny"], s0["R"], seed=W.BASE_SEED + 1)
+    sim = oracle.OracleSim(s0["nx"], s0["ny"], tau=s0["tau"], **C6)
+    sim.set_fields(rho)
+    steps_per = 20   # each benchmark step: 20 time steps of lattice 0 (bounded sample)
+    for _ in range(args.warmup):
+        sim.step(steps_per)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.step(steps_per)
+    dt = time.perf_counter() - t0
+    sites = s0["nx"] * s0["ny"]
+    v = sites * steps_per * args.steps / dt / 1e6
+    out = {
+        "impl": "reference", "metric": "2-species MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "laplace_sweep_24", "sample": "lattice 0 (128x128, R=10, ratio 1), 20 time steps per step",
+                   "precision": "fp64 (CPU oracle)"},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"lattice 0 of the sweep, {steps_per} time steps per benchmark step"},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---- GPU arm ------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, local, world = dist_env()
+    import torch
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    from paper_1806_06943_gb300 import build
+    if rank == 0:
+        build.build()
+    barrier(dist)
+    from paper_1806_06943_gb300 import lb
+
+    stream = torch.cuda.Stream(device=dev)
+    sptr = stream.cuda_stream
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    peak, peak_kind = measured_peaks()
+
+    specs, fields = sweep_fields()
+    sites = sum(s["nx"] * s["ny"] for s in specs)
+    b = make_batch(lb, specs, fields, lb.LB_FP32, sptr)
+
+    # warm-up (untimed), then the timed region: K steps, barrier + sync on both sides
+    b.profile(args.warmup, flush.data_ptr(), FLUSH_BYTES)
+    clocks = ClockSampler(torch.cuda.current_device() if world == 1 else local)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    ms = b.profile(args.steps, flush.data_ptr(), FLUSH_BYTES)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    barrier(dist)
+    # keep sampling clocks over a sustained stretch of the same kernels
+    b.step(2048)
+    b.synchronize()
+    clk = clocks.stop()
+    obs = b.observables()
+
+    ms_step = max_over_ranks(dist, ms[2], dev)
+    value = sum_over_ranks(dist, sites, dev) / (ms_step * 1e-3) / 1e6
+    gpu_launches = 2 * args.steps
+
+    out = {
+        "metric": "2-species MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "laplace_sweep_24", "lattices": len(specs), "sites": sites,
+                   "sizes": "128^2..384^2, R 10..45, mu_d/mu_c 1, 3, 10 (tau_c = 1)",
+                   "precision": "fp32 offset populations, fp64 reductions",
+                   "couplings": C6, "l2": "flushed (256 MiB write) before every timed step",
+                   "timing": "CUDA events per kernel on the launching stream", "parallelism": f"replicas x{world}"},
+        "clocks": clk,
+        "gpu_launches": gpu_launches,
+        "roofline": {
+            "bound": "hbm", "kernel": "k_collide<float> (fused force+collide+stream)",
+            "achieved": BYTES_COLLIDE[1] * sites / (ms[1] * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": BYTES_COLLIDE[1] * sites / (ms[1] * 1e-3) / 1e9 / peak, "traffic": None,
+            "peak_source": f"{peak_kind} hbm_gbs (burst)",
+            "algorithmic_bytes_per_site": BYTES_COLLIDE[1], "units_per_launch": sites,
+            "ms_per_launch": ms[1],
+        },
+        "density_pass": {"ms_per_launch": ms[0], "algorithmic_bytes_per_site": BYTES_DENSITY[1],
+                         "achieved_gbs": BYTES_DENSITY[1] * sites / (ms[0] * 1e-3) / 1e9},
+        "wall_s_timed": t_wall,
+        "observables_after": {"finite": all(o["finite"] == 1.0 for o in obs),
+                              "gamma_fit_ratio1": None},
+    }
+
+    if not args.quick:
+        # sustained rate through the public step call (CUDA graphs, no flush)
+        b.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            b.step(256)
+            ev1.record(stream)
+        ev1.synchronize()
+        out["graph_sustained_mlups"] = sites * 256 / (ev0.elapsed_time(ev1) * 1e-3) / 1e6
+
+        # Laplace fit at ratio 1 after the run so far (not converged; sanity only)
+        # FP64 on the same batch
+        b64 = make_batch(lb, specs, fields, lb.LB_FP64, sptr)
+        b64.profile(3, flush.data_ptr(), FLUSH_BYTES)
+        k64 = max(10, args.steps // 4)
+        ms64 = b64.profile(k64, flush.data_ptr(), FLUSH_BYTES)
+        out["fp64_same_workload"] = {
+            "mlups": sites / (ms64[2] * 1e-3) / 1e6, "ms_per_step": ms64[2], "steps": k64,
+            "collide_ms": ms64[1], "density_ms": ms64[0],
+            "collide_achieved_gbs": BYTES_COLLIDE[0] * sites / (ms64[1] * 1e-3) / 1e9,
+        }
+        out["fp32_over_fp64"] = value / out["fp64_same_workload"]["mlups"]
+        del b64
+
+        # large dense emulsion, 4096^2, FP32 offset and FP64
+        from paper_1806_06943_gb300 import workloads as W
+        rho4k, _, radii, phi = W.random_emulsion(4096, 4096, 0.6, 8.0, 20.0, seed=W.BASE_SEED + 4)
+        big = {"phi_achieved": phi, "droplets": len(radii)}
+        for prec, name in ((lb.LB_FP32, "fp32"), (lb.LB_FP64, "fp64")):
+            L = lb.Lattice(4096, 4096, tau=(3.0, 1.0), precision=prec, rho_ref=(1.0, 1.0), stream=sptr, **C6)
+            L.set_fields(rho4k)
+            L.profile(3)
+            k = 20 if prec == lb.LB_FP32 else 8
+            m = L.profile(k)
+            n4 = 4096 * 4096
+            big[name] = {"mlups": n4 / (m[2] * 1e-3) / 1e6, "ms_per_step": m[2], "steps": k,
+                         "collide_ms": m[1], "density_ms": m[0],
+                         "collide_achieved_gbs": BYTES_COLLIDE[prec] * n4 / (m[1] * 1e-3) / 1e9,
+                         "collide_frac_of_measured_hbm": BYTES_COLLIDE[prec] * n4 / (m[1] * 1e-3) / 1e9 / peak,
+                         "step_effective_gbs_floor": (144 if prec else 288) * n4 / (m[2] * 1e-3) / 1e9}
+            del L
+        out["large_dense_4096"] = big
+
+        # end to end through the public API with host buffers: per e2e step,
+        # upload every lattice's initial fields from pinned host memory, run
+        # 100 time steps, read back the observables of all 24 lattices
+        pinned = [torch.from_numpy(f).pin_memory().numpy() for f in fields]
+        S = 100
+        e2e_iters = 3
+        be = lb.Batch([dict(nx=s["nx"], ny=s["ny"], tau=s["tau"]) for s in specs], precision=lb.LB_FP32,
+                      rho_ref=(1.0, 1.0), stream=sptr, **C6)
+        for i in range(len(specs)):
+            be.set_fields(i, pinned[i])
+        be.step(S)
+        be.observables()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_iters):
+            for i in range(len(specs)):
+                be.set_fields(i, pinned[i])
+            be.step(S)
+            be.observables()
+        dt = time.perf_counter() - t0
+        h2d = sum(f.nbytes for f in pinned)
+        out["e2e"] = {"value": sites * S * e2e_iters / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": 24 * 16 * 8,
+                      "step": f"upload fields of all 24 lattices + {S} time steps + observables readback"}
+        out["gpu_launches"] = gpu_launches
+        del be
+
+        # CPU oracle on a bounded sample (rank 0 only)
+        if rank == 0 and world == 1:
+            v, sample, n = oracle_sample(12.0)
+            out["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

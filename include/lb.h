@@ -1,0 +1,223 @@
+/*
+ * lb.h -- C-ABI of the GB300 two-range pseudopotential lattice Boltzmann
+ * library for binary mixtures with tunable viscosity ratio
+ * (Fei, Scagliarini, Montessori, Lauricella, Succi, Luo, arXiv:1806.06943).
+ *
+ * The method (Sec. II of the paper), per time step and for both species
+ * k in {A, B}:
+ *   rho_k = sum_i f_k,i                                 Eq. (6)
+ *   psi_k = 1 - exp(-rho_k)                             Sec. II B
+ *   F_k   = F^c_k (Eq. 8, D2Q9 + D2Q25 stencils) + F^r_k (Eq. 9) + rho_k g
+ *   rho_k u_k = sum_i f_k,i e_i + F_k / 2               Eq. (6)
+ *   u^eq  = sum_k (rho_k u_k / tau_k) / sum_k (rho_k / tau_k)     Eq. (3)
+ *   f_k,i(x + e_i, t + 1) = f - (f - f^eq(rho_k, u^eq)) / tau_k + C^Guo_k,i
+ *                                                      Eqs. (1), (2), (5)
+ * with half-way bounce-back walls at y = -1/2 and y = ny - 1/2 (Sec. III A)
+ * and periodic boundaries otherwise.
+ *
+ * Conventions shared by every call:
+ *  - Host arrays are row-major, x fastest: a field is [ny][nx] doubles and a
+ *    species-resolved field is [2][ny][nx] (species A first).  A vector field
+ *    stores its x component block before its y component block.
+ *  - Calls return LB_OK (0) or a negative error code; the message of the
+ *    last failure on the calling thread is returned by lb_last_error().  No
+ *    call aborts, traps or exits the process.
+ *  - Work is enqueued on lb_params.stream when it is not NULL (a stream the
+ *    caller created on the current device; not the legacy default stream,
+ *    since the time loop is replayed as a captured CUDA graph), otherwise on
+ *    a non-blocking stream the handle creates and owns.  Calls that return
+ *    host data synchronise that stream.
+ *  - The handle owns all device memory it uses; the caller owns every
+ *    pointer it passes and may reuse it as soon as the call returns.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define LB_OK 0
+#define LB_EINVAL (-1)    /* invalid argument: tau <= 1/2, nx or ny < 5, non-finite parameter, bad pointer */
+#define LB_ENOMEM (-2)    /* device or host allocation failed */
+#define LB_ECUDA (-3)     /* a CUDA runtime call failed (message names it) */
+#define LB_EUNSTABLE (-4) /* a density or velocity became non-finite */
+#define LB_ETIMEOUT (-5)  /* a bounded device-side wait expired */
+
+/* Number formats of the populations. */
+#define LB_FP64 0         /* plain populations f in IEEE double */
+#define LB_FP32 1         /* offset populations g = f - w_i rho_ref_k in IEEE single */
+
+/* Wall configurations. */
+#define LB_PERIODIC 0     /* periodic in x and y */
+#define LB_WALLS_Y 1      /* half-way bounce-back walls at y = -1/2 and y = ny - 1/2, periodic in x */
+
+/* Densities the interaction stencils see beyond a wall (ghost rows
+ * y = -1, -2 and y = ny, ny + 1). */
+#define LB_WALL_MIRROR 0  /* row -1 <- row 0, row -2 <- row 1, and symmetrically at the top */
+#define LB_WALL_FIXED 1   /* wall_rho[k] for species k (non-wetting walls, Sec. III D) */
+
+/* Parameters of one lattice (Sec. II A-B; Sec. III for the walls).
+ *   nx, ny     lattice size, both >= 5
+ *   tau[k]     relaxation times tau_A, tau_B > 1/2; nu_k = (tau_k - 1/2)/3
+ *   G_AB       inter-species repulsion strength (Eq. 9), G_AB = G_BA
+ *   G1, G2     short-range and mid-range intra-species strengths (Eq. 8),
+ *              the same for both species
+ *   g[2]       body acceleration; the body force on species k is rho_k g
+ *   walls      LB_PERIODIC or LB_WALLS_Y
+ *   wall_mode  LB_WALL_MIRROR or LB_WALL_FIXED (ignored without walls)
+ *   wall_rho   ghost densities for LB_WALL_FIXED
+ *   precision  LB_FP64 or LB_FP32
+ *   rho_ref    offsets rho_ref_k of the LB_FP32 populations (ignored for LB_FP64)
+ *   stream     the cudaStream_t to run on (see above), or NULL */
+typedef struct lb_params {
+    int32_t nx, ny;
+    double tau[2];
+    double G_AB, G1, G2;
+    double g[2];
+    int32_t walls;
+    int32_t wall_mode;
+    double wall_rho[2];
+    int32_t precision;
+    int32_t reserved;
+    double rho_ref[2];
+    void *stream;
+} lb_params;
+
+/* Observables at the current time t, computed from the pre-collision
+ * populations and the forces recomputed from them; sums in FP64.
+ *   mass[k]      sum_x rho_k
+ *   mom[k][a]    sum_x rho_k u_k,a (half force included, Eq. 6)
+ *   flux_Q       (1/nx) sum_x ubar_x, ubar the barycentric velocity (Eq. 7)
+ *   mu_r         Q0 / flux_Q, Q0 = g_x (ny^3 + ny/2) / (12 nu_B) the flux of
+ *                the pure continuous phase (Sec. III D); NaN without walls
+ *                or with g_x = 0
+ *   dp_laplace   <p_b>_in - <p_b>_out around the probe (Eq. 11 bulk
+ *                pressure; inside r < R/2, outside r > R + 6); NaN without probe
+ *   R_eff        equimolar radius of species A around the probe; NaN without probe
+ *   umax         max_x |ubar|
+ *   finite       1 if every density and velocity is finite, else 0 */
+typedef struct lb_obs {
+    int64_t t;
+    double mass[2];
+    double mom[2][2];
+    double flux_Q;
+    double mu_r;
+    double dp_laplace;
+    double R_eff;
+    double umax;
+    int32_t finite;
+    int32_t reserved;
+} lb_obs;
+
+typedef struct lb_handle lb_handle;
+typedef struct lb_batch lb_batch;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *lb_last_error(void);
+
+/* ---- one lattice ----------------------------------------------------------- */
+
+/* Create a lattice on the current CUDA device.  The parameters are copied.
+ * Populations start at f = f^eq(rho = 0, u = 0); set them with
+ * lb_set_fields before stepping.  Returns LB_EINVAL, LB_ENOMEM or LB_ECUDA on
+ * failure, with *out set to NULL. */
+int lb_create(const lb_params *p, lb_handle **out);
+
+/* Free the lattice and all its device memory.  NULL is ignored. */
+void lb_destroy(lb_handle *h);
+
+/* Set f_k,i = f^eq_i(rho_k, u) (Eq. 2) at every node and t = 0.
+ *   rho  host [2][ny][nx] species densities
+ *   u    host [2][ny][nx] initial velocity (x block, then y block), or NULL for rest
+ * Synchronous with respect to the host buffers. */
+int lb_set_fields(lb_handle *h, const double *rho, const double *u);
+
+/* As lb_set_fields, with rho and u in device memory of the handle's device;
+ * the copy is ordered on the handle's stream. */
+int lb_set_fields_device(lb_handle *h, const double *rho, const double *u);
+
+/* Advance n >= 0 time steps.  Asynchronous: returns once the work is
+ * enqueued; a failure detected on the device surfaces on the next
+ * synchronising call (lb_observables, lb_get_fields, lb_synchronize). */
+int lb_step(lb_handle *h, int64_t n);
+
+/* Block until the handle's queued work has finished. */
+int lb_synchronize(lb_handle *h);
+
+/* Current time step count. */
+int64_t lb_time(const lb_handle *h);
+
+/* Probe for the Laplace observables: disk centre (cx, cy) and nominal
+ * radius R > 0 (R <= 0 removes the probe). */
+int lb_set_probe(lb_handle *h, double cx, double cy, double R);
+
+/* Compute the observables at the current time into *o.  Synchronises.
+ * Returns LB_EUNSTABLE (with *o filled) if a value is non-finite. */
+int lb_observables(lb_handle *h, lb_obs *o);
+
+/* Copy diagnostic fields at the current time to host memory; NULL skips one.
+ *   rho   [2][ny][nx]       species densities
+ *   mom   [2][2][ny][nx]    species momenta rho_k u_k with half force (Eq. 6)
+ *   ubar  [2][ny][nx]       barycentric velocity (Eq. 7)
+ * Synchronises. */
+int lb_get_fields(lb_handle *h, double *rho, double *mom, double *ubar);
+
+/* Copy the populations f_k,i (as FP64, offsets added back for LB_FP32) to
+ * host [2][9][ny][nx], direction order: rest, (1,0), (0,1), (-1,0), (0,-1),
+ * (1,1), (-1,1), (-1,-1), (1,-1).  Synchronises. */
+int lb_get_populations(lb_handle *h, double *f);
+
+/* Overwrite the populations from host [2][9][ny][nx] (same order) and set the
+ * time counter to t. */
+int lb_set_populations(lb_handle *h, const double *f, int64_t t);
+
+/* Checkpoint: with buf == NULL store the byte size needed in *len; otherwise
+ * write the time counter and the raw populations (bitwise, native format)
+ * into buf of *len bytes.  Synchronises. */
+int lb_save(lb_handle *h, void *buf, size_t *len);
+
+/* Restore a checkpoint written by lb_save on a lattice of the same size and
+ * precision. */
+int lb_load(lb_handle *h, const void *buf, size_t len);
+
+/* Time nsteps time steps kernel by kernel with CUDA events on the handle's
+ * stream (direct launches, no graph):
+ *   ms[0]  mean duration of one density-pass launch
+ *   ms[1]  mean duration of one fused force/collide/stream launch
+ *   ms[2]  mean duration of one whole time step (both launches)
+ * If flush_bytes > 0, the caller's device buffer flush_buf of that size is
+ * overwritten before every step, outside the timed intervals, so that each
+ * step starts with no population data in L2.  The lattice advances by
+ * nsteps.  Synchronises. */
+int lb_profile(lb_handle *h, int32_t nsteps, void *flush_buf, size_t flush_bytes, double ms[3]);
+
+/* ---- many independent lattices advanced together ------------------------- */
+
+/* Create n >= 1 lattices of possibly different sizes and parameters that
+ * are stepped together: each time step is one launch of each kernel over the
+ * tiles of all lattices.  All p[i].precision must agree; the stream of p[0]
+ * is used. */
+int lb_batch_create(const lb_params *p, int32_t n, lb_batch **out);
+void lb_batch_destroy(lb_batch *b);
+int lb_batch_size(const lb_batch *b);
+int lb_batch_set_fields(lb_batch *b, int32_t i, const double *rho, const double *u);
+int lb_batch_step(lb_batch *b, int64_t n);
+int lb_batch_synchronize(lb_batch *b);
+int lb_batch_set_probe(lb_batch *b, int32_t i, double cx, double cy, double R);
+/* o points to n lb_obs, one per lattice.  Synchronises. */
+int lb_batch_observables(lb_batch *b, lb_obs *o);
+int lb_batch_get_fields(lb_batch *b, int32_t i, double *rho, double *mom, double *ubar);
+/* As lb_profile, over all lattices of the batch (one launch covers them all). */
+int lb_batch_profile(lb_batch *b, int32_t nsteps, void *flush_buf, size_t flush_bytes, double ms[3]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_H */

@@ -1,0 +1,767 @@
+// lb_api.cu -- C-ABI of the lattice Boltzmann library (declared in lb.h):
+// parameter validation, device memory, tile lists, stream ordering, CUDA-graph
+// replay of the time loop, and host<->device transfers.  All arithmetic of the
+// method runs in the kernels of lb_kernels.cuh.
+//
+// Host code of this file is compiled with -ffp-contract=off so the derived
+// FP64 parameters (1/tau, (1 - 1/(2 tau)) w) round exactly as written.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lb.h"
+#include "lb_kernels.cuh"
+#include "lb_launch.h"
+#include "lb_types.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(LB_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LB_CUDA(call)                                    \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+constexpr int kGraphSteps = 32;   // steps per captured graph (even: parity returns)
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool is_fin(double v) { return std::isfinite(v); }
+
+int validate(const lb_params *p, int i)
+{
+    char buf[160];
+    if (!p) return fail(LB_EINVAL, "params is NULL");
+    if (p->nx < 5 || p->ny < 5) {
+        snprintf(buf, sizeof buf, "lattice %d: nx=%d ny=%d, both must be >= 5", i, p->nx, p->ny);
+        return fail(LB_EINVAL, buf);
+    }
+    if ((long long)p->nx * p->ny > (1ll << 31)) return fail(LB_EINVAL, "lattice too large (nx*ny > 2^31)");
+    for (int k = 0; k < 2; ++k)
+        if (!is_fin(p->tau[k]) || !(p->tau[k] > 0.5)) {
+            snprintf(buf, sizeof buf, "lattice %d: tau[%d]=%g must be finite and > 1/2", i, k, p->tau[k]);
+            return fail(LB_EINVAL, buf);
+        }
+    const double vals[] = {p->G_AB, p->G1, p->G2, p->g[0], p->g[1], p->wall_rho[0], p->wall_rho[1], p->rho_ref[0],
+                           p->rho_ref[1]};
+    for (double v : vals)
+        if (!is_fin(v)) return fail(LB_EINVAL, "non-finite coupling, force, wall density or offset");
+    if (p->walls != LB_PERIODIC && p->walls != LB_WALLS_Y) return fail(LB_EINVAL, "walls must be 0 or 1");
+    if (p->wall_mode != LB_WALL_MIRROR && p->wall_mode != LB_WALL_FIXED) return fail(LB_EINVAL, "wall_mode must be 0 or 1");
+    if (p->precision != LB_FP64 && p->precision != LB_FP32) return fail(LB_EINVAL, "precision must be LB_FP64 or LB_FP32");
+    return LB_OK;
+}
+
+template <typename real>
+void fill_lat(lbk::Lat<real> &L, const lb_params &p)
+{
+    std::memset(&L, 0, sizeof L);
+    L.nx = p.nx;
+    L.ny = p.ny;
+    L.pitch = (int)align_up((size_t)p.nx, 32);
+    L.plane = (size_t)L.pitch * p.ny;
+    L.walls = p.walls;
+    L.wall_mode = p.wall_mode;
+    const double wcls[3] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0};
+    for (int k = 0; k < 2; ++k) {
+        const double omega = 1.0 / p.tau[k];
+        L.omega[k] = (real)omega;
+        for (int c = 0; c < 3; ++c) L.aw[k][c] = (real)((1.0 - 0.5 * omega) * wcls[c]);
+        L.g[k] = (real)p.g[k];
+        L.wall_rho[k] = (real)p.wall_rho[k];
+        L.rho_ref[k] = sizeof(real) == 8 ? (real)0 : (real)p.rho_ref[k];
+    }
+    L.G1 = (real)p.G1;
+    L.G2 = (real)p.G2;
+    L.GAB = (real)p.G_AB;
+    L.tau_B = p.tau[1];
+    L.g_x = p.g[0];
+}
+
+}  // namespace
+
+struct lb_engine {
+    int precision = LB_FP64;
+    int n = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;   // the caller's stream, or one the engine owns
+    bool own_stream = false;
+    std::vector<lb_params> P;
+    std::vector<lbk::Lat<double>> L64;
+    std::vector<lbk::Lat<float>> L32;
+    std::vector<int4> tiles;
+    void *d_lats = nullptr;
+    int4 *d_tiles = nullptr;
+    void *d_pool = nullptr;
+    double *d_partials = nullptr;
+    double *d_obs = nullptr;
+    double *d_tmp = nullptr;
+    size_t tmp_elems = 0;
+    int64_t t = 0;
+    int parity = 0;
+    cudaGraphExec_t gexec = nullptr;
+
+    ~lb_engine()
+    {
+        if (stream) cudaStreamSynchronize(stream);
+        if (gexec) cudaGraphExecDestroy(gexec);
+        cudaFree(d_lats);
+        cudaFree(d_tiles);
+        cudaFree(d_pool);
+        cudaFree(d_partials);
+        cudaFree(d_obs);
+        cudaFree(d_tmp);
+        if (stream && own_stream) cudaStreamDestroy(stream);
+    }
+
+    size_t real_size() const { return precision == LB_FP64 ? 8 : 4; }
+    int nx(int l) const { return P[l].nx; }
+    int ny(int l) const { return P[l].ny; }
+    int tile_begin(int l) const { return precision == LB_FP64 ? L64[l].tile_begin : L32[l].tile_begin; }
+    int tile_end(int l) const { return precision == LB_FP64 ? L64[l].tile_end : L32[l].tile_end; }
+    size_t plane(int l) const { return precision == LB_FP64 ? L64[l].plane : L32[l].plane; }
+    void *fbuf(int l, int par) const
+    {
+        return precision == LB_FP64 ? (void *)L64[l].f[par] : (void *)L32[l].f[par];
+    }
+
+    int begin()
+    {
+        if (cudaSetDevice(device) != cudaSuccess) return fail(LB_ECUDA, "cudaSetDevice failed");
+        return LB_OK;
+    }
+    int end() { return LB_OK; }
+
+    cudaError_t launch_density(int par, int off, int cnt)
+    {
+        if (precision == LB_FP64)
+            return lbk::Launch<double>::density((const lbk::Lat<double> *)d_lats, d_tiles, off, cnt, par, stream);
+        return lbk::Launch<float>::density((const lbk::Lat<float> *)d_lats, d_tiles, off, cnt, par, stream);
+    }
+    cudaError_t launch_collide(int par, int off, int cnt)
+    {
+        if (precision == LB_FP64)
+            return lbk::Launch<double>::collide((const lbk::Lat<double> *)d_lats, d_tiles, off, cnt, par, stream);
+        return lbk::Launch<float>::collide((const lbk::Lat<float> *)d_lats, d_tiles, off, cnt, par, stream);
+    }
+    cudaError_t launch_step(int par)
+    {
+        const int nt = (int)tiles.size();
+        cudaError_t e = launch_density(par, 0, nt);
+        if (e != cudaSuccess) return e;
+        return launch_collide(par, 0, nt);
+    }
+    cudaError_t launch_observe(int par, int off, int cnt, double *partials, double *rho, double *mom, double *ubar)
+    {
+        if (precision == LB_FP64)
+            return lbk::Launch<double>::observe((const lbk::Lat<double> *)d_lats, d_tiles, off, cnt, par, partials,
+                                                rho, mom, ubar, stream);
+        return lbk::Launch<float>::observe((const lbk::Lat<float> *)d_lats, d_tiles, off, cnt, par, partials, rho,
+                                           mom, ubar, stream);
+    }
+    cudaError_t launch_finalize()
+    {
+        if (precision == LB_FP64)
+            return lbk::Launch<double>::finalize((const lbk::Lat<double> *)d_lats, n, d_partials, d_obs, stream);
+        return lbk::Launch<float>::finalize((const lbk::Lat<float> *)d_lats, n, d_partials, d_obs, stream);
+    }
+
+    int ensure_tmp(size_t elems)
+    {
+        if (elems <= tmp_elems) return LB_OK;
+        if (d_tmp) {
+            LB_CUDA(cudaStreamSynchronize(stream));
+            cudaFree(d_tmp);
+            d_tmp = nullptr;
+            tmp_elems = 0;
+        }
+        if (cudaMalloc(&d_tmp, elems * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LB_ENOMEM, "cudaMalloc of the transfer buffer failed");
+        }
+        tmp_elems = elems;
+        return LB_OK;
+    }
+
+    int build_graph()
+    {
+        cudaGraph_t g = nullptr;
+        LB_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = cudaSuccess;
+        for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s) le = launch_step(s & 1);
+        cudaError_t ce = cudaStreamEndCapture(stream, &g);
+        if (le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(le, "kernel launch during graph capture");
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        cudaError_t ie = cudaGraphInstantiate(&gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            gexec = nullptr;
+            return cuda_fail(ie, "cudaGraphInstantiate");
+        }
+        return LB_OK;
+    }
+
+    int step(int64_t nsteps)
+    {
+        if (nsteps < 0) return fail(LB_EINVAL, "negative step count");
+        int rc = begin();
+        if (rc) return rc;
+        while (nsteps > 0) {
+            if (parity == 0 && nsteps >= kGraphSteps) {
+                if (!gexec && (rc = build_graph())) return rc;
+                LB_CUDA(cudaGraphLaunch(gexec, stream));
+                nsteps -= kGraphSteps;
+                t += kGraphSteps;
+            } else {
+                LB_CUDA(launch_step(parity));
+                parity ^= 1;
+                nsteps -= 1;
+                t += 1;
+            }
+        }
+        return end();
+    }
+
+    int profile(int32_t nsteps, void *flush, size_t flush_bytes, double ms[3])
+    {
+        if (nsteps < 1 || !ms) return fail(LB_EINVAL, "profile needs nsteps >= 1 and ms");
+        if (flush_bytes > 0 && !flush) return fail(LB_EINVAL, "flush_bytes > 0 with a NULL flush buffer");
+        int rc = begin();
+        if (rc) return rc;
+        std::vector<cudaEvent_t> ev(3 * (size_t)nsteps, nullptr);
+        auto cleanup = [&]() {
+            for (auto &x : ev)
+                if (x) cudaEventDestroy(x);
+        };
+        for (auto &x : ev)
+            if (cudaEventCreate(&x) != cudaSuccess) {
+                cleanup();
+                return fail(LB_ECUDA, "cudaEventCreate failed");
+            }
+        const int nt = (int)tiles.size();
+        cudaError_t ce = cudaSuccess;
+        for (int s = 0; s < nsteps && ce == cudaSuccess; ++s) {
+            if (flush_bytes) ce = cudaMemsetAsync(flush, s & 0xff, flush_bytes, stream);
+            if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s], stream);
+            if (ce == cudaSuccess) ce = launch_density(parity, 0, nt);
+            if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s + 1], stream);
+            if (ce == cudaSuccess) ce = launch_collide(parity, 0, nt);
+            if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s + 2], stream);
+            if (ce == cudaSuccess) {
+                parity ^= 1;
+                t += 1;
+            }
+        }
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int s = 0; s < nsteps && ce == cudaSuccess; ++s) {
+            float a = 0.f, b = 0.f, c = 0.f;
+            ce = cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]);
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&b, ev[3 * s + 1], ev[3 * s + 2]);
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&c, ev[3 * s], ev[3 * s + 2]);
+            acc[0] += a;
+            acc[1] += b;
+            acc[2] += c;
+        }
+        cleanup();
+        if (ce != cudaSuccess) return cuda_fail(ce, "profiled time steps");
+        for (int k = 0; k < 3; ++k) ms[k] = acc[k] / nsteps;
+        return end();
+    }
+
+    int observables(lb_obs *o)
+    {
+        int rc = begin();
+        if (rc) return rc;
+        const int nt = (int)tiles.size();
+        LB_CUDA(launch_density(parity, 0, nt));
+        LB_CUDA(launch_observe(parity, 0, nt, d_partials, nullptr, nullptr, nullptr));
+        LB_CUDA(launch_finalize());
+        std::vector<double> h((size_t)n * lbk::kObsStride);
+        LB_CUDA(cudaMemcpyAsync(h.data(), d_obs, h.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        LB_CUDA(cudaStreamSynchronize(stream));
+        bool all_finite = true;
+        for (int l = 0; l < n; ++l) {
+            const double *s = &h[(size_t)l * lbk::kObsStride];
+            lb_obs &r = o[l];
+            std::memset(&r, 0, sizeof r);
+            r.t = t;
+            r.mass[0] = s[lbk::oMassA];
+            r.mass[1] = s[lbk::oMassB];
+            r.mom[0][0] = s[lbk::oMomAx];
+            r.mom[0][1] = s[lbk::oMomAy];
+            r.mom[1][0] = s[lbk::oMomBx];
+            r.mom[1][1] = s[lbk::oMomBy];
+            r.flux_Q = s[lbk::oQ];
+            r.mu_r = s[lbk::oMuR];
+            r.dp_laplace = s[lbk::oDp];
+            r.R_eff = s[lbk::oReff];
+            r.umax = s[lbk::oUmax];
+            r.finite = s[lbk::oFinite] != 0.0 ? 1 : 0;
+            all_finite = all_finite && r.finite;
+        }
+        rc = end();
+        if (rc) return rc;
+        if (!all_finite) return fail(LB_EUNSTABLE, "a density or velocity is not finite");
+        return LB_OK;
+    }
+
+    int get_fields(int l, double *rho, double *mom, double *ubar)
+    {
+        const size_t cells = (size_t)nx(l) * ny(l);
+        int rc = begin();
+        if (rc) return rc;
+        if ((rc = ensure_tmp(8 * cells))) return rc;
+        LB_CUDA(launch_density(parity, tile_begin(l), tile_end(l) - tile_begin(l)));
+        LB_CUDA(launch_observe(parity, tile_begin(l), tile_end(l) - tile_begin(l), nullptr, d_tmp, d_tmp + 2 * cells,
+                               d_tmp + 6 * cells));
+        if (rho) LB_CUDA(cudaMemcpyAsync(rho, d_tmp, 2 * cells * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        if (mom)
+            LB_CUDA(cudaMemcpyAsync(mom, d_tmp + 2 * cells, 4 * cells * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        if (ubar)
+            LB_CUDA(cudaMemcpyAsync(ubar, d_tmp + 6 * cells, 2 * cells * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        LB_CUDA(cudaStreamSynchronize(stream));
+        return end();
+    }
+
+    int set_fields(int l, const double *rho, const double *u, bool device_ptrs)
+    {
+        if (!rho) return fail(LB_EINVAL, "rho is NULL");
+        const size_t cells = (size_t)nx(l) * ny(l);
+        int rc = begin();
+        if (rc) return rc;
+        const double *drho = rho, *du = u;
+        if (!device_ptrs) {
+            if ((rc = ensure_tmp(4 * cells))) return rc;
+            LB_CUDA(cudaMemcpyAsync(d_tmp, rho, 2 * cells * sizeof(double), cudaMemcpyHostToDevice, stream));
+            drho = d_tmp;
+            du = nullptr;
+            if (u) {
+                LB_CUDA(cudaMemcpyAsync(d_tmp + 2 * cells, u, 2 * cells * sizeof(double), cudaMemcpyHostToDevice,
+                                        stream));
+                du = d_tmp + 2 * cells;
+            }
+        }
+        if (precision == LB_FP64)
+            LB_CUDA(lbk::Launch<double>::init((const lbk::Lat<double> *)d_lats, l, nx(l), ny(l), drho, du, parity, stream));
+        else
+            LB_CUDA(lbk::Launch<float>::init((const lbk::Lat<float> *)d_lats, l, nx(l), ny(l), drho, du, parity, stream));
+        if (!device_ptrs) LB_CUDA(cudaStreamSynchronize(stream));
+        return end();
+    }
+
+    int get_pops(int l, double *f)
+    {
+        if (!f) return fail(LB_EINVAL, "f is NULL");
+        const size_t cells = (size_t)nx(l) * ny(l);
+        int rc = begin();
+        if (rc) return rc;
+        if ((rc = ensure_tmp(18 * cells))) return rc;
+        if (precision == LB_FP64)
+            LB_CUDA(lbk::Launch<double>::get_pops((const lbk::Lat<double> *)d_lats, l, nx(l), ny(l), parity, d_tmp, stream));
+        else
+            LB_CUDA(lbk::Launch<float>::get_pops((const lbk::Lat<float> *)d_lats, l, nx(l), ny(l), parity, d_tmp, stream));
+        LB_CUDA(cudaMemcpyAsync(f, d_tmp, 18 * cells * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        LB_CUDA(cudaStreamSynchronize(stream));
+        return end();
+    }
+
+    int set_pops(int l, const double *f)
+    {
+        if (!f) return fail(LB_EINVAL, "f is NULL");
+        const size_t cells = (size_t)nx(l) * ny(l);
+        int rc = begin();
+        if (rc) return rc;
+        if ((rc = ensure_tmp(18 * cells))) return rc;
+        LB_CUDA(cudaMemcpyAsync(d_tmp, f, 18 * cells * sizeof(double), cudaMemcpyHostToDevice, stream));
+        if (precision == LB_FP64)
+            LB_CUDA(lbk::Launch<double>::set_pops((const lbk::Lat<double> *)d_lats, l, nx(l), ny(l), parity, d_tmp, stream));
+        else
+            LB_CUDA(lbk::Launch<float>::set_pops((const lbk::Lat<float> *)d_lats, l, nx(l), ny(l), parity, d_tmp, stream));
+        LB_CUDA(cudaStreamSynchronize(stream));
+        return end();
+    }
+
+    int set_probe(int l, double cx, double cy, double R)
+    {
+        if (!is_fin(cx) || !is_fin(cy) || !is_fin(R)) return fail(LB_EINVAL, "non-finite probe");
+        int rc = begin();
+        if (rc) return rc;
+        const int has = R > 0.0 ? 1 : 0;
+        const double pr[3] = {cx, cy, R};
+        if (precision == LB_FP64) {
+            L64[l].has_probe = has;
+            std::memcpy(L64[l].probe, pr, sizeof pr);
+            LB_CUDA(cudaMemcpyAsync((lbk::Lat<double> *)d_lats + l, &L64[l], sizeof(L64[l]), cudaMemcpyHostToDevice,
+                                    stream));
+        } else {
+            L32[l].has_probe = has;
+            std::memcpy(L32[l].probe, pr, sizeof pr);
+            LB_CUDA(cudaMemcpyAsync((lbk::Lat<float> *)d_lats + l, &L32[l], sizeof(L32[l]), cudaMemcpyHostToDevice,
+                                    stream));
+        }
+        LB_CUDA(cudaStreamSynchronize(stream));
+        return end();
+    }
+};
+
+namespace {
+
+int engine_create(const lb_params *p, int n, lb_engine **out)
+{
+    *out = nullptr;
+    if (n < 1) return fail(LB_EINVAL, "need at least one lattice");
+    for (int i = 0; i < n; ++i) {
+        int rc = validate(&p[i], i);
+        if (rc) return rc;
+        if (p[i].precision != p[0].precision) return fail(LB_EINVAL, "all lattices of a batch need the same precision");
+    }
+    lb_engine *e = new (std::nothrow) lb_engine();
+    if (!e) return fail(LB_ENOMEM, "host allocation failed");
+    e->precision = p[0].precision;
+    e->n = n;
+    e->P.assign(p, p + n);
+    auto bail = [&](int rc) {
+        delete e;
+        return rc;
+    };
+    if (cudaGetDevice(&e->device) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(LB_ECUDA, "no CUDA device"));
+    }
+    cudaError_t ce;
+    if (p[0].stream) {
+        e->stream = (cudaStream_t)p[0].stream;
+    } else {
+        if ((ce = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(cuda_fail(ce, "cudaStreamCreateWithFlags"));
+        e->own_stream = true;
+    }
+
+    // layout: per lattice two population copies and the density field
+    const size_t rs = e->real_size();
+    std::vector<size_t> off_f0(n), off_f1(n), off_rho(n);
+    size_t total = 0;
+    for (int l = 0; l < n; ++l) {
+        const size_t pitch = align_up((size_t)p[l].nx, 32), plane = pitch * p[l].ny;
+        off_f0[l] = total;
+        total = align_up(total + 18 * plane * rs, kAlign);
+        off_f1[l] = total;
+        total = align_up(total + 18 * plane * rs, kAlign);
+        off_rho[l] = total;
+        total = align_up(total + 2 * plane * rs, kAlign);
+    }
+    if (cudaMalloc(&e->d_pool, total) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(LB_ENOMEM, "cudaMalloc of the lattice state failed"));
+    }
+    if ((ce = cudaMemsetAsync(e->d_pool, 0, total, e->stream)) != cudaSuccess) return bail(cuda_fail(ce, "cudaMemsetAsync"));
+
+    // tiles in raster order, lattice by lattice
+    for (int l = 0; l < n; ++l) {
+        const int begin = (int)e->tiles.size();
+        for (int y0 = 0; y0 < p[l].ny; y0 += lbk::TY)
+            for (int x0 = 0; x0 < p[l].nx; x0 += lbk::TX) e->tiles.push_back(make_int4(l, x0, y0, 0));
+        const int end = (int)e->tiles.size();
+        char *base = (char *)e->d_pool;
+        if (e->precision == LB_FP64) {
+            lbk::Lat<double> L;
+            fill_lat(L, p[l]);
+            L.f[0] = (double *)(base + off_f0[l]);
+            L.f[1] = (double *)(base + off_f1[l]);
+            L.rho = (double *)(base + off_rho[l]);
+            L.tile_begin = begin;
+            L.tile_end = end;
+            e->L64.push_back(L);
+        } else {
+            lbk::Lat<float> L;
+            fill_lat(L, p[l]);
+            L.f[0] = (float *)(base + off_f0[l]);
+            L.f[1] = (float *)(base + off_f1[l]);
+            L.rho = (float *)(base + off_rho[l]);
+            L.tile_begin = begin;
+            L.tile_end = end;
+            e->L32.push_back(L);
+        }
+    }
+    const size_t lat_bytes = e->precision == LB_FP64 ? n * sizeof(lbk::Lat<double>) : n * sizeof(lbk::Lat<float>);
+    const void *lat_src = e->precision == LB_FP64 ? (const void *)e->L64.data() : (const void *)e->L32.data();
+    if (cudaMalloc(&e->d_lats, lat_bytes) != cudaSuccess ||
+        cudaMalloc((void **)&e->d_tiles, e->tiles.size() * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc((void **)&e->d_partials, e->tiles.size() * lbk::kAccStride * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&e->d_obs, (size_t)n * lbk::kObsStride * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(LB_ENOMEM, "cudaMalloc of the descriptors failed"));
+    }
+    if ((ce = cudaMemcpyAsync(e->d_lats, lat_src, lat_bytes, cudaMemcpyHostToDevice, e->stream)) != cudaSuccess ||
+        (ce = cudaMemcpyAsync(e->d_tiles, e->tiles.data(), e->tiles.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                              e->stream)) != cudaSuccess ||
+        (ce = cudaStreamSynchronize(e->stream)) != cudaSuccess)
+        return bail(cuda_fail(ce, "descriptor upload"));
+    *out = e;
+    return LB_OK;
+}
+
+struct SaveHeader {
+    char magic[8];
+    int32_t precision, nx, ny, pad;
+    int64_t t;
+    int64_t bytes;
+};
+
+}  // namespace
+
+struct lb_handle {
+    lb_engine *e;
+};
+struct lb_batch {
+    lb_engine *e;
+};
+
+extern "C" {
+
+const char *lb_last_error(void) { return g_err.c_str(); }
+
+int lb_create(const lb_params *p, lb_handle **out)
+{
+    if (!out) return fail(LB_EINVAL, "out is NULL");
+    *out = nullptr;
+    lb_engine *e = nullptr;
+    int rc = engine_create(p, 1, &e);
+    if (rc) return rc;
+    lb_handle *h = new (std::nothrow) lb_handle{e};
+    if (!h) {
+        delete e;
+        return fail(LB_ENOMEM, "host allocation failed");
+    }
+    *out = h;
+    return LB_OK;
+}
+
+void lb_destroy(lb_handle *h)
+{
+    if (!h) return;
+    delete h->e;
+    delete h;
+}
+
+#define CHECK_H(h) \
+    if (!(h) || !(h)->e) return fail(LB_EINVAL, "handle is NULL")
+
+int lb_set_fields(lb_handle *h, const double *rho, const double *u)
+{
+    CHECK_H(h);
+    int rc = h->e->set_fields(0, rho, u, false);
+    if (!rc) h->e->t = 0;
+    return rc;
+}
+
+int lb_set_fields_device(lb_handle *h, const double *rho, const double *u)
+{
+    CHECK_H(h);
+    int rc = h->e->set_fields(0, rho, u, true);
+    if (!rc) h->e->t = 0;
+    return rc;
+}
+
+int lb_step(lb_handle *h, int64_t n)
+{
+    CHECK_H(h);
+    return h->e->step(n);
+}
+
+int lb_synchronize(lb_handle *h)
+{
+    CHECK_H(h);
+    cudaError_t ce = cudaStreamSynchronize(h->e->stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
+    return LB_OK;
+}
+
+int64_t lb_time(const lb_handle *h) { return (h && h->e) ? h->e->t : -1; }
+
+int lb_set_probe(lb_handle *h, double cx, double cy, double R)
+{
+    CHECK_H(h);
+    return h->e->set_probe(0, cx, cy, R);
+}
+
+int lb_observables(lb_handle *h, lb_obs *o)
+{
+    CHECK_H(h);
+    if (!o) return fail(LB_EINVAL, "o is NULL");
+    return h->e->observables(o);
+}
+
+int lb_get_fields(lb_handle *h, double *rho, double *mom, double *ubar)
+{
+    CHECK_H(h);
+    return h->e->get_fields(0, rho, mom, ubar);
+}
+
+int lb_get_populations(lb_handle *h, double *f)
+{
+    CHECK_H(h);
+    return h->e->get_pops(0, f);
+}
+
+int lb_set_populations(lb_handle *h, const double *f, int64_t t)
+{
+    CHECK_H(h);
+    int rc = h->e->set_pops(0, f);
+    if (!rc) h->e->t = t;
+    return rc;
+}
+
+int lb_save(lb_handle *h, void *buf, size_t *len)
+{
+    CHECK_H(h);
+    if (!len) return fail(LB_EINVAL, "len is NULL");
+    lb_engine *e = h->e;
+    const size_t bytes = 18 * e->plane(0) * e->real_size();
+    const size_t need = sizeof(SaveHeader) + bytes;
+    if (!buf) {
+        *len = need;
+        return LB_OK;
+    }
+    if (*len < need) return fail(LB_EINVAL, "checkpoint buffer too small");
+    SaveHeader hd;
+    std::memset(&hd, 0, sizeof hd);
+    std::memcpy(hd.magic, "LBGB300", 8);
+    hd.precision = e->precision;
+    hd.nx = e->nx(0);
+    hd.ny = e->ny(0);
+    hd.t = e->t;
+    hd.bytes = (int64_t)bytes;
+    std::memcpy(buf, &hd, sizeof hd);
+    int rc = e->begin();
+    if (rc) return rc;
+    LB_CUDA(cudaMemcpyAsync((char *)buf + sizeof hd, e->fbuf(0, e->parity), bytes, cudaMemcpyDeviceToHost, e->stream));
+    LB_CUDA(cudaStreamSynchronize(e->stream));
+    *len = need;
+    return e->end();
+}
+
+int lb_load(lb_handle *h, const void *buf, size_t len)
+{
+    CHECK_H(h);
+    if (!buf || len < sizeof(SaveHeader)) return fail(LB_EINVAL, "checkpoint buffer too small");
+    lb_engine *e = h->e;
+    SaveHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    const size_t bytes = 18 * e->plane(0) * e->real_size();
+    if (std::memcmp(hd.magic, "LBGB300", 8) != 0 || hd.precision != e->precision || hd.nx != e->nx(0) ||
+        hd.ny != e->ny(0) || (size_t)hd.bytes != bytes || len < sizeof hd + bytes)
+        return fail(LB_EINVAL, "checkpoint does not match this lattice");
+    int rc = e->begin();
+    if (rc) return rc;
+    LB_CUDA(cudaMemcpyAsync(e->fbuf(0, e->parity), (const char *)buf + sizeof hd, bytes, cudaMemcpyHostToDevice,
+                            e->stream));
+    LB_CUDA(cudaStreamSynchronize(e->stream));
+    e->t = hd.t;
+    return e->end();
+}
+
+int lb_profile(lb_handle *h, int32_t nsteps, void *flush_buf, size_t flush_bytes, double ms[3])
+{
+    CHECK_H(h);
+    return h->e->profile(nsteps, flush_buf, flush_bytes, ms);
+}
+
+int lb_batch_create(const lb_params *p, int32_t n, lb_batch **out)
+{
+    if (!out) return fail(LB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(LB_EINVAL, "params is NULL");
+    lb_engine *e = nullptr;
+    int rc = engine_create(p, n, &e);
+    if (rc) return rc;
+    lb_batch *b = new (std::nothrow) lb_batch{e};
+    if (!b) {
+        delete e;
+        return fail(LB_ENOMEM, "host allocation failed");
+    }
+    *out = b;
+    return LB_OK;
+}
+
+void lb_batch_destroy(lb_batch *b)
+{
+    if (!b) return;
+    delete b->e;
+    delete b;
+}
+
+#define CHECK_B(b, i)                                                           \
+    if (!(b) || !(b)->e) return fail(LB_EINVAL, "batch is NULL");               \
+    if ((i) < 0 || (i) >= (b)->e->n) return fail(LB_EINVAL, "lattice index out of range")
+
+int lb_batch_size(const lb_batch *b) { return (b && b->e) ? b->e->n : -1; }
+
+int lb_batch_set_fields(lb_batch *b, int32_t i, const double *rho, const double *u)
+{
+    CHECK_B(b, i);
+    return b->e->set_fields(i, rho, u, false);
+}
+
+int lb_batch_step(lb_batch *b, int64_t n)
+{
+    CHECK_B(b, 0);
+    return b->e->step(n);
+}
+
+int lb_batch_synchronize(lb_batch *b)
+{
+    CHECK_B(b, 0);
+    cudaError_t ce = cudaStreamSynchronize(b->e->stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
+    return LB_OK;
+}
+
+int lb_batch_set_probe(lb_batch *b, int32_t i, double cx, double cy, double R)
+{
+    CHECK_B(b, i);
+    return b->e->set_probe(i, cx, cy, R);
+}
+
+int lb_batch_observables(lb_batch *b, lb_obs *o)
+{
+    CHECK_B(b, 0);
+    if (!o) return fail(LB_EINVAL, "o is NULL");
+    return b->e->observables(o);
+}
+
+int lb_batch_get_fields(lb_batch *b, int32_t i, double *rho, double *mom, double *ubar)
+{
+    CHECK_B(b, i);
+    return b->e->get_fields(i, rho, mom, ubar);
+}
+
+int lb_batch_profile(lb_batch *b, int32_t nsteps, void *flush_buf, size_t flush_bytes, double ms[3])
+{
+    CHECK_B(b, 0);
+    return b->e->profile(nsteps, flush_buf, flush_bytes, ms);
+}
+
+}  // extern "C"

@@ -1,0 +1,542 @@
+// lb_kernels.cuh -- sm_103a kernels of the two-range pseudopotential lattice
+// Boltzmann step (Fei et al., arXiv:1806.06943, Sec. II), templated on the
+// population format:
+//   real = double : plain populations f; this instantiation is compiled
+//                   without fused multiply-add and evaluates every sum in the
+//                   same order as the step's definition below, so it reproduces
+//                   a straightforward FP64 evaluation of the equations up to
+//                   the last bit of exp().
+//   real = float  : offset populations g = f - w_i rho_ref_k; rho_k = rho_ref_k
+//                   + sum_i g; FMA contraction allowed.
+//
+// One time step is two launches over a list of tiles (lattice, x0, y0):
+//   k_density : rho_k = sum_i f_k,i                           (Eq. 6)
+//   k_collide : stages rho_k of the tile plus a 2-node halo in shared memory,
+//               psi_k = 1 - exp(-rho_k) (Sec. II B), the forces of Eqs. (8),
+//               (9) and rho_k g, the moments of Eq. (6), u^eq of Eq. (3), the
+//               BGK relaxation to Eq. (2) with the Guo term of Eq. (5), and
+//               pushes each post-collision population to x + e_i, reflecting
+//               it at a half-way bounce-back wall (Sec. III A).
+// The populations at a node are the pre-collision values of the current time,
+// so both passes read them at their own node with coalesced loads.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "lb_types.h"
+
+namespace lbk {
+
+constexpr int TX = 32;           // tile width = threads in x
+constexpr int TY = 8;            // tile height = threads in y
+constexpr int HALO = 2;          // reach of the D2Q25 stencil
+constexpr int SW = TX + 2 * HALO;
+constexpr int SH = TY + 2 * HALO;
+constexpr int kThreads = TX * TY;
+
+// ---- lattice tables (Sec. II A; Fig. 1; Sec. II B after Eq. 8) ------------
+// D2Q9 order: rest, (1,0), (0,1), (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1).
+__host__ __device__ constexpr int ex9(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
+__host__ __device__ constexpr int ey9(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
+__host__ __device__ constexpr int opp9(int i)
+{
+    return i == 0 ? 0 : i == 1 ? 3 : i == 2 ? 4 : i == 3 ? 1 : i == 4 ? 2 : i == 5 ? 7 : i == 6 ? 8 : i == 7 ? 5 : 6;
+}
+// w(|e|^2) class of direction i: 0 rest, 1 axis, 2 diagonal.
+__host__ __device__ constexpr int cls9(int i) { return i == 0 ? 0 : (i <= 4 ? 1 : 2); }
+__host__ __device__ constexpr double w9(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+// D2Q25 weights p(|e|^2).
+__host__ __device__ constexpr double p25(int e2)
+{
+    return e2 == 0 ? 247.0 / 420.0 : e2 == 1 ? 4.0 / 63.0 : e2 == 2 ? 4.0 / 135.0 : e2 == 4 ? 1.0 / 180.0
+         : e2 == 5 ? 2.0 / 945.0 : e2 == 8 ? 1.0 / 15120.0 : 0.0;
+}
+
+template <typename real> __device__ __forceinline__ real psi_of(real r);
+// psi = rho0 (1 - exp(-rho/rho0)), rho0 = 1 (Sec. II B)
+template <> __device__ __forceinline__ double psi_of<double>(double r) { return 1.0 - exp(-r); }
+// same function, written through expm1 so small densities keep their digits
+template <> __device__ __forceinline__ float psi_of<float>(float r) { return -expm1f(-r); }
+
+__device__ __forceinline__ int wrap_index(int a, int n)
+{
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+// Stage rho_k and psi_k of the tile plus its halo into shared memory.
+// Periodic copies in x (and in y without walls); beyond a wall the ghost rows
+// are either mirrored from the fluid or set to the fixed wall densities.
+template <typename real>
+__device__ __forceinline__ void stage_tile(const Lat<real> &L, int x0, int y0,
+                                           real (*srho)[SH][SW], real (*spsi)[SH][SW], int tid, int nthreads)
+{
+    const int nx = L.nx, ny = L.ny;
+    for (int idx = tid; idx < SW * SH; idx += nthreads) {
+        const int sx = idx % SW, sy = idx / SW;
+        const int gx = wrap_index(x0 + sx - HALO, nx);
+        int gy = y0 + sy - HALO;
+        real rA, rB;
+        bool fixed = false;
+        if (gy < 0 || gy >= ny) {
+            if (L.walls) {
+                if (L.wall_mode == 1) {
+                    rA = L.wall_rho[0];
+                    rB = L.wall_rho[1];
+                    fixed = true;
+                } else {
+                    gy = gy < 0 ? -1 - gy : 2 * ny - 1 - gy;
+                    gy = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);  // rows no valid node reads
+                }
+            } else {
+                gy = wrap_index(gy, ny);
+            }
+        }
+        if (!fixed) {
+            const size_t c = (size_t)gy * L.pitch + gx;
+            rA = L.rho[c];
+            rB = L.rho[L.plane + c];
+        }
+        srho[0][sy][sx] = rA;
+        srho[1][sy][sx] = rB;
+        spsi[0][sy][sx] = psi_of<real>(rA);
+        spsi[1][sy][sx] = psi_of<real>(rB);
+    }
+}
+
+// sum_{i=1..8} w_i s(x + e_i) e_i, added in direction order (Eqs. 8, 9).
+template <typename real>
+__device__ __forceinline__ void q9_sum(const real (*s)[SW], int cx, int cy, real &sx, real &sy)
+{
+    const real W1 = (real)(1.0 / 9.0), W2 = (real)(1.0 / 36.0);
+    const real a1 = W1 * s[cy][cx + 1], a2 = W1 * s[cy + 1][cx], a3 = W1 * s[cy][cx - 1], a4 = W1 * s[cy - 1][cx];
+    const real a5 = W2 * s[cy + 1][cx + 1], a6 = W2 * s[cy + 1][cx - 1];
+    const real a7 = W2 * s[cy - 1][cx - 1], a8 = W2 * s[cy - 1][cx + 1];
+    sx = ((((a1 - a3) + a5) - a6) - a7) + a8;
+    sy = ((((a2 - a4) + a5) + a6) - a7) - a8;
+}
+
+// sum_{j} p_j s(x + e_j) e_j over D2Q25 in raster order (dy outer, dx inner).
+template <typename real>
+__device__ __forceinline__ void q25_sum(const real (*s)[SW], int cx, int cy, real &sx, real &sy)
+{
+    sx = (real)0;
+    sy = (real)0;
+#pragma unroll
+    for (int j = 0; j < 25; ++j) {
+        const int dx = j % 5 - 2, dy = j / 5 - 2;
+        if (dx == 0 && dy == 0) continue;
+        const real pp = (real)p25(dx * dx + dy * dy) * s[cy + dy][cx + dx];
+        if (dx != 0) sx += pp * (real)dx;
+        if (dy != 0) sy += pp * (real)dy;
+    }
+}
+
+// Total force on species k at the staged node (cx, cy): Eq. (8) + Eq. (9) + rho_k g.
+template <typename real>
+__device__ __forceinline__ void force_at(const Lat<real> &L, const real (*srho)[SH][SW], const real (*spsi)[SH][SW],
+                                         int k, int cx, int cy, real &Fx, real &Fy)
+{
+    real s1x, s1y, s2x, s2y, s3x, s3y;
+    q9_sum<real>(spsi[k], cx, cy, s1x, s1y);
+    q25_sum<real>(spsi[k], cx, cy, s2x, s2y);
+    q9_sum<real>(srho[1 - k], cx, cy, s3x, s3y);
+    const real psi = spsi[k][cy][cx], rho = srho[k][cy][cx];
+    const real G1 = L.G1, G2 = L.G2, GAB = L.GAB;
+    Fx = -G1 * psi * s1x - G2 * psi * s2x - GAB * rho * s3x + rho * L.g[0];
+    Fy = -G1 * psi * s1y - G2 * psi * s2y - GAB * rho * s3y + rho * L.g[1];
+}
+
+// e_i . u in the order e_x u_x + e_y u_y, zero products dropped.
+template <typename real, int EX, int EY>
+__device__ __forceinline__ real edot(real ux, real uy)
+{
+    if constexpr (EX == 0 && EY == 0) return (real)0;
+    else if constexpr (EX == 0) return EY > 0 ? uy : -uy;
+    else if constexpr (EY == 0) return EX > 0 ? ux : -ux;
+    else return (EX > 0 ? ux : -ux) + (EY > 0 ? uy : -uy);
+}
+
+// (e_a - u_a)/cs^2 + (e.u) e_a / cs^4 for one component a.
+template <typename real, int E>
+__device__ __forceinline__ real guo_comp(real u, real eu)
+{
+    if constexpr (E == 0) return -((real)3 * u);
+    else if constexpr (E > 0) return (real)3 * ((real)1 - u) + (real)9 * eu;
+    else return (real)3 * ((real)-1 - u) - (real)9 * eu;
+}
+
+// BGK relaxation with Guo forcing for direction I of one species
+// (Eqs. 1, 2, 5).  FP64: plain population; FP32: offset population with
+// delta = rho - rho_ref.
+template <typename real, int I>
+__device__ __forceinline__ real collide_dir(real f, real rho, real delta, real ux, real uy, real uu,
+                                            real Fx, real Fy, real om, real aw)
+{
+    constexpr int EX = ex9(I), EY = ey9(I);
+    const real w = (real)w9(I);
+    const real eu = edot<real, EX, EY>(ux, uy);
+    const real C = aw * (guo_comp<real, EX>(ux, eu) * Fx + guo_comp<real, EY>(uy, eu) * Fy);
+    if constexpr (sizeof(real) == 8) {
+        (void)delta;
+        const real feq = w * rho * ((real)1 + (real)3 * eu + (real)4.5 * eu * eu - (real)1.5 * uu);
+        return f - om * (f - feq) + C;
+    } else {
+        const real geq = w * (delta + rho * ((real)3 * eu + (real)4.5 * eu * eu - (real)1.5 * uu));
+        return f - om * (f - geq) + C;
+    }
+}
+
+template <typename real, int I>
+__device__ __forceinline__ void push_dir(const Lat<real> &L, real *__restrict__ fn, int k, int x, int y, real v)
+{
+    constexpr int EX = ex9(I), EY = ey9(I);
+    int xd = x + EX, yd = y + EY;
+    if constexpr (EX != 0) {
+        if (xd >= L.nx) xd -= L.nx;
+        if (xd < 0) xd += L.nx;
+    }
+    int dir = I;
+    if constexpr (EY != 0) {
+        if (yd < 0 || yd >= L.ny) {
+            if (L.walls) {       // half-way bounce-back: back to this node, reversed
+                dir = opp9(I);
+                xd = x;
+                yd = y;
+            } else {
+                yd = yd < 0 ? yd + L.ny : yd - L.ny;
+            }
+        }
+    }
+    fn[(size_t)(k * 9 + dir) * L.plane + (size_t)yd * L.pitch + xd] = v;
+}
+
+template <typename real, int I>
+__device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__restrict__ fn, const real (&fk)[2][9],
+                                                 const real (&rho)[2], const real (&delta)[2], real ux, real uy, real uu,
+                                                 const real (&F)[2][2], int x, int y)
+{
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const real v = collide_dir<real, I>(fk[k][I], rho[k], delta[k], ux, uy, uu, F[k][0], F[k][1], L.omega[k],
+                                            L.aw[k][cls9(I)]);
+        push_dir<real, I>(L, fn, k, x, y, v);
+    }
+}
+
+// Species momentum sum_i f e_i in direction order, zero products dropped.
+template <typename real>
+__device__ __forceinline__ void first_moment(const real (&f)[9], real &jx, real &jy)
+{
+    jx = ((((f[1] - f[3]) + f[5]) - f[6]) - f[7]) + f[8];
+    jy = ((((f[2] - f[4]) + f[5]) + f[6]) - f[7]) - f[8];
+}
+
+template <typename real>
+__device__ __forceinline__ real zeroth_moment(const real (&f)[9])
+{
+    return (((((((f[0] + f[1]) + f[2]) + f[3]) + f[4]) + f[5]) + f[6]) + f[7]) + f[8];
+}
+
+// ---- kernels ----------------------------------------------------------------
+
+// rho_k = sum_i f_k,i (FP32: rho_ref_k + sum_i g_k,i).
+template <typename real>
+__global__ void __launch_bounds__(kThreads) k_density(const Lat<real> *__restrict__ lats, const int4 *__restrict__ tiles,
+                                                      int tile_offset, int parity)
+{
+    const int4 t = tiles[tile_offset + blockIdx.x];
+    const Lat<real> &L = lats[t.x];
+    const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
+    if (x >= L.nx || y >= L.ny) return;
+    const real *__restrict__ f = L.f[parity];
+    const size_t c = (size_t)y * L.pitch + x;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        real v[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) v[i] = f[(size_t)(k * 9 + i) * L.plane + c];
+        real r = zeroth_moment<real>(v);
+        if constexpr (sizeof(real) == 4) r = L.rho_ref[k] + r;
+        L.rho[(size_t)k * L.plane + c] = r;
+    }
+}
+
+// Fused force + collision + push-streaming + bounce-back for one tile.
+template <typename real>
+__global__ void __launch_bounds__(kThreads) k_collide(const Lat<real> *__restrict__ lats, const int4 *__restrict__ tiles,
+                                                      int tile_offset, int parity)
+{
+    __shared__ real srho[2][SH][SW];
+    __shared__ real spsi[2][SH][SW];
+    const int4 t = tiles[tile_offset + blockIdx.x];
+    const Lat<real> &L = lats[t.x];
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    stage_tile<real>(L, t.y, t.z, srho, spsi, tid, kThreads);
+    __syncthreads();
+    const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
+    if (x >= L.nx || y >= L.ny) return;
+    const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
+
+    const real *__restrict__ fc = L.f[parity];
+    real *__restrict__ fn = L.f[parity ^ 1];
+    const size_t c = (size_t)y * L.pitch + x;
+    real fk[2][9];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fk[k][i] = fc[(size_t)(k * 9 + i) * L.plane + c];
+
+    real F[2][2], rho[2], delta[2], m[2][2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        force_at<real>(L, srho, spsi, k, cx, cy, F[k][0], F[k][1]);
+        rho[k] = srho[k][cy][cx];
+        delta[k] = (sizeof(real) == 4) ? zeroth_moment<real>(fk[k]) : (real)0;
+        real jx, jy;
+        first_moment<real>(fk[k], jx, jy);
+        m[k][0] = jx + (real)0.5 * F[k][0];   // Eq. (6), half force
+        m[k][1] = jy + (real)0.5 * F[k][1];
+    }
+    // common velocity, Eq. (3)
+    const real om0 = L.omega[0], om1 = L.omega[1];
+    const real den = om0 * rho[0] + om1 * rho[1];
+    const real ux = (om0 * m[0][0] + om1 * m[1][0]) / den;
+    const real uy = (om0 * m[0][1] + om1 * m[1][1]) / den;
+    const real uu = ux * ux + uy * uy;
+
+    collide_push_dir<real, 0>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
+    collide_push_dir<real, 1>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
+    collide_push_dir<real, 2>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
+    collide_push_dir<real, 3>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
+    collide_push_dir<real, 4>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
+    collide_push_dir<real, 5>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
+    collide_push_dir<real, 6>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
+    collide_push_dir<real, 7>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
+    collide_push_dir<real, 8>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
+}
+
+// ---- observables ------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Per-node diagnostics (densities, momenta with half force, barycentric
+// velocity, Eq. 11 bulk pressure) reduced per tile into FP64 partial sums;
+// optionally also written as dense FP64 fields [..][ny][nx].
+template <typename real>
+__global__ void __launch_bounds__(kThreads) k_observe(const Lat<real> *__restrict__ lats, const int4 *__restrict__ tiles,
+                                                      int tile_offset, int parity, double *__restrict__ partials,
+                                                      double *__restrict__ out_rho, double *__restrict__ out_mom,
+                                                      double *__restrict__ out_ubar)
+{
+    __shared__ real srho[2][SH][SW];
+    __shared__ real spsi[2][SH][SW];
+    __shared__ double sacc[kThreads / 32][kAccStride];
+    const int4 t = tiles[tile_offset + blockIdx.x];
+    const Lat<real> &L = lats[t.x];
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    stage_tile<real>(L, t.y, t.z, srho, spsi, tid, kThreads);
+    __syncthreads();
+    const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
+    double acc[kNumAcc];
+#pragma unroll
+    for (int a = 0; a < kNumAcc; ++a) acc[a] = 0.0;
+    if (x < L.nx && y < L.ny) {
+        const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
+        const real *__restrict__ fc = L.f[parity];
+        const size_t c = (size_t)y * L.pitch + x;
+        double r[2], m[2][2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            real fk[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fk[i] = fc[(size_t)(k * 9 + i) * L.plane + c];
+            real Fx, Fy, jx, jy;
+            force_at<real>(L, srho, spsi, k, cx, cy, Fx, Fy);
+            first_moment<real>(fk, jx, jy);
+            r[k] = (double)srho[k][cy][cx];
+            m[k][0] = (double)(jx + (real)0.5 * Fx);
+            m[k][1] = (double)(jy + (real)0.5 * Fy);
+        }
+        const double rt = r[0] + r[1];
+        const double ux = (m[0][0] + m[1][0]) / rt, uy = (m[0][1] + m[1][1]) / rt;
+        acc[kMassA] = r[0];
+        acc[kMassB] = r[1];
+        acc[kMomAx] = m[0][0];
+        acc[kMomAy] = m[0][1];
+        acc[kMomBx] = m[1][0];
+        acc[kMomBy] = m[1][1];
+        acc[kSumUx] = ux;
+        acc[kUmax] = sqrt(ux * ux + uy * uy);
+        acc[kNonFinite] = (isfinite(r[0]) && isfinite(r[1]) && isfinite(ux) && isfinite(uy)) ? 0.0 : 1.0;
+        if (L.has_probe) {
+            double dx = fabs((double)x - L.probe[0]), dy = fabs((double)y - L.probe[1]);
+            if (dx > 0.5 * L.nx) dx = L.nx - dx;
+            if (!L.walls && dy > 0.5 * L.ny) dy = L.ny - dy;
+            const double rr = sqrt(dx * dx + dy * dy), R = L.probe[2];
+            const double psiA = 1.0 - exp(-r[0]), psiB = 1.0 - exp(-r[1]);
+            const double Gs = (double)L.G1 + (double)L.G2;
+            const double pb = (r[0] + 0.5 * Gs * psiA * psiA) / 3.0 + (r[1] + 0.5 * Gs * psiB * psiB) / 3.0
+                            + (double)L.GAB * r[0] * r[1] / 3.0;
+            if (rr < 0.5 * R) { acc[kPIn] = pb; acc[kAIn] = r[0]; acc[kNIn] = 1.0; }
+            if (rr > R + 6.0) { acc[kPOut] = pb; acc[kAOut] = r[0]; acc[kNOut] = 1.0; }
+        }
+        if (out_rho) {
+            const size_t n = (size_t)L.nx * L.ny, d = (size_t)y * L.nx + x;
+            out_rho[d] = r[0];
+            out_rho[n + d] = r[1];
+            if (out_mom) {
+                out_mom[d] = m[0][0];
+                out_mom[n + d] = m[0][1];
+                out_mom[2 * n + d] = m[1][0];
+                out_mom[3 * n + d] = m[1][1];
+            }
+            if (out_ubar) {
+                out_ubar[d] = ux;
+                out_ubar[n + d] = uy;
+            }
+        }
+    }
+    if (!partials) return;
+    const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int a = 0; a < kNumAcc; ++a) {
+        const double v = (a == kUmax) ? warp_max(acc[a]) : warp_sum(acc[a]);
+        if (lane == 0) sacc[warp][a] = v;
+    }
+    __syncthreads();
+    if (tid < kNumAcc) {
+        double v = sacc[0][tid];
+        for (int w = 1; w < kThreads / 32; ++w) v = (tid == kUmax) ? fmax(v, sacc[w][tid]) : v + sacc[w][tid];
+        partials[(size_t)(tile_offset + blockIdx.x) * kAccStride + tid] = v;
+    }
+}
+
+// One block per lattice: reduce its tile partials in a fixed order and
+// derive the observables.
+template <typename real>
+__global__ void __launch_bounds__(256) k_finalize(const Lat<real> *__restrict__ lats, const double *__restrict__ partials,
+                                                  double *__restrict__ obs)
+{
+    __shared__ double sred[256 / 32][kAccStride];
+    const Lat<real> &L = lats[blockIdx.x];
+    const int tid = threadIdx.x;
+    double acc[kNumAcc];
+#pragma unroll
+    for (int a = 0; a < kNumAcc; ++a) acc[a] = 0.0;
+    for (int tl = L.tile_begin + tid; tl < L.tile_end; tl += 256) {
+#pragma unroll
+        for (int a = 0; a < kNumAcc; ++a) {
+            const double v = partials[(size_t)tl * kAccStride + a];
+            acc[a] = (a == kUmax) ? fmax(acc[a], v) : acc[a] + v;
+        }
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int a = 0; a < kNumAcc; ++a) {
+        const double v = (a == kUmax) ? warp_max(acc[a]) : warp_sum(acc[a]);
+        if (lane == 0) sred[warp][a] = v;
+    }
+    __syncthreads();
+    if (tid != 0) return;
+    double s[kNumAcc];
+    for (int a = 0; a < kNumAcc; ++a) {
+        double v = sred[0][a];
+        for (int w = 1; w < 8; ++w) v = (a == kUmax) ? fmax(v, sred[w][a]) : v + sred[w][a];
+        s[a] = v;
+    }
+    double *o = obs + (size_t)blockIdx.x * kObsStride;
+    o[oMassA] = s[kMassA];
+    o[oMassB] = s[kMassB];
+    o[oMomAx] = s[kMomAx];
+    o[oMomAy] = s[kMomAy];
+    o[oMomBx] = s[kMomBx];
+    o[oMomBy] = s[kMomBy];
+    o[oQ] = s[kSumUx] / L.nx;
+    if (L.walls && L.g_x != 0.0) {
+        const double H = L.ny, nuB = (L.tau_B - 0.5) / 3.0;
+        const double Q0 = L.g_x * (H * H * H + 0.5 * H) / (12.0 * nuB);
+        o[oMuR] = Q0 / o[oQ];
+    } else {
+        o[oMuR] = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    if (L.has_probe && s[kNIn] > 0.0 && s[kNOut] > 0.0) {
+        const double rin = s[kAIn] / s[kNIn], rout = s[kAOut] / s[kNOut];
+        o[oDp] = s[kPIn] / s[kNIn] - s[kPOut] / s[kNOut];
+        o[oReff] = sqrt((s[kMassA] - rout * (double)L.nx * (double)L.ny) / (3.14159265358979323846 * (rin - rout)));
+    } else {
+        o[oDp] = __longlong_as_double(0x7ff8000000000000ll);
+        o[oReff] = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    o[oUmax] = s[kUmax];
+    o[oFinite] = s[kNonFinite] == 0.0 ? 1.0 : 0.0;
+}
+
+// ---- initialisation and population transfer ---------------------------------
+
+// f_k,i = f^eq_i(rho_k, u) (Eq. 2) from dense FP64 fields; FP32 stores the
+// offset f^eq - w_i rho_ref_k.
+template <typename real>
+__global__ void k_init(const Lat<real> *__restrict__ lats, int lat, const double *__restrict__ rho,
+                       const double *__restrict__ u, int parity)
+{
+    const Lat<real> &L = lats[lat];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx || y >= L.ny) return;
+    const size_t n = (size_t)L.nx * L.ny, d = (size_t)y * L.nx + x;
+    const double ux = u ? u[d] : 0.0, uy = u ? u[n + d] : 0.0;
+    const double uu = ux * ux + uy * uy;
+    real *f = L.f[parity];
+    const size_t c = (size_t)y * L.pitch + x;
+    for (int k = 0; k < 2; ++k) {
+        const double r = rho[k * n + d];
+        for (int i = 0; i < 9; ++i) {
+            const double eu = ex9(i) * ux + ey9(i) * uy;
+            const double feq = w9(i) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+            f[(size_t)(k * 9 + i) * L.plane + c] = (real)(feq - w9(i) * (double)L.rho_ref[k]);
+        }
+    }
+}
+
+// dense FP64 [2][9][ny][nx] <-> native pitched populations (offsets added back
+// or removed for FP32).
+template <typename real>
+__global__ void k_get_pops(const Lat<real> *__restrict__ lats, int lat, int parity, double *__restrict__ out)
+{
+    const Lat<real> &L = lats[lat];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx || y >= L.ny) return;
+    const size_t n = (size_t)L.nx * L.ny, d = (size_t)y * L.nx + x, c = (size_t)y * L.pitch + x;
+    for (int k = 0; k < 2; ++k)
+        for (int i = 0; i < 9; ++i)
+            out[(size_t)(k * 9 + i) * n + d] =
+                (double)L.f[parity][(size_t)(k * 9 + i) * L.plane + c] + w9(i) * (double)L.rho_ref[k];
+}
+
+template <typename real>
+__global__ void k_set_pops(const Lat<real> *__restrict__ lats, int lat, int parity, const double *__restrict__ in)
+{
+    const Lat<real> &L = lats[lat];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx || y >= L.ny) return;
+    const size_t n = (size_t)L.nx * L.ny, d = (size_t)y * L.nx + x, c = (size_t)y * L.pitch + x;
+    for (int k = 0; k < 2; ++k)
+        for (int i = 0; i < 9; ++i)
+            L.f[parity][(size_t)(k * 9 + i) * L.plane + c] =
+                (real)(in[(size_t)(k * 9 + i) * n + d] - w9(i) * (double)L.rho_ref[k]);
+}
+
+}  // namespace lbk

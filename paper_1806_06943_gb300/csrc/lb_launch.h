@@ -1,0 +1,32 @@
+// lb_launch.h -- host-side launchers of the lattice Boltzmann kernels, one
+// explicit instantiation per population format (lb_fp64.cu, lb_fp32.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lb_types.h"
+
+namespace lbk {
+
+template <typename real>
+struct Launch {
+    // one kernel launch over tiles [tile_offset, tile_offset + n_tiles)
+    static cudaError_t density(const Lat<real> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
+                               cudaStream_t s);
+    static cudaError_t collide(const Lat<real> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
+                               cudaStream_t s);
+    static cudaError_t observe(const Lat<real> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
+                               double *partials, double *rho, double *mom, double *ubar, cudaStream_t s);
+    static cudaError_t finalize(const Lat<real> *lats, int n_lat, const double *partials, double *obs, cudaStream_t s);
+    // one lattice, dense FP64 host-layout buffers in device memory
+    static cudaError_t init(const Lat<real> *lats, int lat, int nx, int ny, const double *rho, const double *u,
+                            int parity, cudaStream_t s);
+    static cudaError_t get_pops(const Lat<real> *lats, int lat, int nx, int ny, int parity, double *out, cudaStream_t s);
+    static cudaError_t set_pops(const Lat<real> *lats, int lat, int nx, int ny, int parity, const double *in,
+                                cudaStream_t s);
+};
+
+extern template struct Launch<double>;
+extern template struct Launch<float>;
+
+}  // namespace lbk
