@@ -102,7 +102,7 @@ def sweep_fields():
 
 def make_batch(lb, specs, fields, precision, stream):
     b = lb.Batch([dict(nx=s["nx"], ny=s["ny"], tau=s["tau"]) for s in specs], precision=precision,
-                 rho_ref=(1.0, 1.0), stream=stream, **C6)
+                 stream=stream, **C6)
     for i, (s, r) in enumerate(zip(specs, fields)):
         b.set_fields(i, r)
         b.set_probe(i, s["nx"] / 2, s["ny"] / 2, s["R"])
@@ -289,7 +289,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": "laplace_sweep_24", "lattices": len(specs), "sites": sites,
                    "sizes": "128^2..384^2, R 10..45, mu_d/mu_c 1, 3, 10 (tau_c = 1)",
-                   "precision": "fp32 offset populations, fp64 reductions",
+                   "precision": "fp32 offset populations (per-node reference density), fp64 reductions",
                    "couplings": C6, "l2": "flushed (256 MiB write) before every timed step",
                    "timing": "CUDA events per kernel on the launching stream", "parallelism": f"replicas x{world}"},
         "clocks": clk,
@@ -339,7 +339,7 @@ def main():
         rho4k, _, radii, phi = W.random_emulsion(4096, 4096, 0.6, 8.0, 20.0, seed=W.BASE_SEED + 4)
         big = {"phi_achieved": phi, "droplets": len(radii)}
         for prec, name in ((lb.LB_FP32, "fp32"), (lb.LB_FP64, "fp64")):
-            L = lb.Lattice(4096, 4096, tau=(3.0, 1.0), precision=prec, rho_ref=(1.0, 1.0), stream=sptr, **C6)
+            L = lb.Lattice(4096, 4096, tau=(3.0, 1.0), precision=prec, stream=sptr, **C6)
             L.set_fields(rho4k)
             L.profile(3)
             k = 20 if prec == lb.LB_FP32 else 8
@@ -360,7 +360,7 @@ def main():
         S = 100
         e2e_iters = 3
         be = lb.Batch([dict(nx=s["nx"], ny=s["ny"], tau=s["tau"]) for s in specs], precision=lb.LB_FP32,
-                      rho_ref=(1.0, 1.0), stream=sptr, **C6)
+                      stream=sptr, **C6)
         for i in range(len(specs)):
             be.set_fields(i, pinned[i])
         be.step(S)

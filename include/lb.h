@@ -51,7 +51,8 @@ extern "C" {
 
 /* Number formats of the populations. */
 #define LB_FP64 0         /* plain populations f in IEEE double */
-#define LB_FP32 1         /* offset populations g = f - w_i rho_ref_k in IEEE single */
+#define LB_FP32 1         /* offset populations h_i = f_i - w_i R in IEEE single, R the node's
+                             density at the previous step; sums of the observables in FP64 */
 
 /* Wall configurations. */
 #define LB_PERIODIC 0     /* periodic in x and y */
@@ -73,7 +74,6 @@ extern "C" {
  *   wall_mode  LB_WALL_MIRROR or LB_WALL_FIXED (ignored without walls)
  *   wall_rho   ghost densities for LB_WALL_FIXED
  *   precision  LB_FP64 or LB_FP32
- *   rho_ref    offsets rho_ref_k of the LB_FP32 populations (ignored for LB_FP64)
  *   stream     the cudaStream_t to run on (see above), or NULL */
 typedef struct lb_params {
     int32_t nx, ny;
@@ -85,7 +85,6 @@ typedef struct lb_params {
     double wall_rho[2];
     int32_t precision;
     int32_t reserved;
-    double rho_ref[2];
     void *stream;
 } lb_params;
 
@@ -168,18 +167,19 @@ int lb_observables(lb_handle *h, lb_obs *o);
  * Synchronises. */
 int lb_get_fields(lb_handle *h, double *rho, double *mom, double *ubar);
 
-/* Copy the populations f_k,i (as FP64, offsets added back for LB_FP32) to
+/* Copy the populations f_k,i (as FP64; for LB_FP32 with w_i R added back) to
  * host [2][9][ny][nx], direction order: rest, (1,0), (0,1), (-1,0), (0,-1),
  * (1,1), (-1,1), (-1,-1), (1,-1).  Synchronises. */
 int lb_get_populations(lb_handle *h, double *f);
 
 /* Overwrite the populations from host [2][9][ny][nx] (same order) and set the
- * time counter to t. */
+ * time counter to t (LB_FP32: R becomes sum_i f_k,i rounded to single). */
 int lb_set_populations(lb_handle *h, const double *f, int64_t t);
 
 /* Checkpoint: with buf == NULL store the byte size needed in *len; otherwise
- * write the time counter and the raw populations (bitwise, native format)
- * into buf of *len bytes.  Synchronises. */
+ * write the time counter and the raw state (populations, and for LB_FP32 the
+ * reference densities; bitwise, native format) into buf of *len bytes.
+ * Synchronises. */
 int lb_save(lb_handle *h, void *buf, size_t *len);
 
 /* Restore a checkpoint written by lb_save on a lattice of the same size and

@@ -60,10 +60,9 @@ int validate(const lb_params *p, int i)
             snprintf(buf, sizeof buf, "lattice %d: tau[%d]=%g must be finite and > 1/2", i, k, p->tau[k]);
             return fail(LB_EINVAL, buf);
         }
-    const double vals[] = {p->G_AB, p->G1, p->G2, p->g[0], p->g[1], p->wall_rho[0], p->wall_rho[1], p->rho_ref[0],
-                           p->rho_ref[1]};
+    const double vals[] = {p->G_AB, p->G1, p->G2, p->g[0], p->g[1], p->wall_rho[0], p->wall_rho[1]};
     for (double v : vals)
-        if (!is_fin(v)) return fail(LB_EINVAL, "non-finite coupling, force, wall density or offset");
+        if (!is_fin(v)) return fail(LB_EINVAL, "non-finite coupling, force or wall density");
     if (p->walls != LB_PERIODIC && p->walls != LB_WALLS_Y) return fail(LB_EINVAL, "walls must be 0 or 1");
     if (p->wall_mode != LB_WALL_MIRROR && p->wall_mode != LB_WALL_FIXED) return fail(LB_EINVAL, "wall_mode must be 0 or 1");
     if (p->precision != LB_FP64 && p->precision != LB_FP32) return fail(LB_EINVAL, "precision must be LB_FP64 or LB_FP32");
@@ -87,7 +86,6 @@ void fill_lat(lbk::Lat<real> &L, const lb_params &p)
         for (int c = 0; c < 3; ++c) L.aw[k][c] = (real)((1.0 - 0.5 * omega) * wcls[c]);
         L.g[k] = (real)p.g[k];
         L.wall_rho[k] = (real)p.wall_rho[k];
-        L.rho_ref[k] = sizeof(real) == 8 ? (real)0 : (real)p.rho_ref[k];
     }
     L.G1 = (real)p.G1;
     L.G2 = (real)p.G2;
@@ -142,6 +140,14 @@ struct lb_engine {
     {
         return precision == LB_FP64 ? (void *)L64[l].f[par] : (void *)L32[l].f[par];
     }
+    void *rbuf(int l, int par) const
+    {
+        return precision == LB_FP64 ? (void *)L64[l].rho[par] : (void *)L32[l].rho[par];
+    }
+    // bytes of the state a checkpoint holds: populations, plus the FP32
+    // reference densities
+    size_t pop_bytes(int l) const { return 18 * plane(l) * real_size(); }
+    size_t ref_bytes(int l) const { return precision == LB_FP32 ? 2 * plane(l) * real_size() : 0; }
 
     int begin()
     {
@@ -461,7 +467,7 @@ int engine_create(const lb_params *p, int n, lb_engine **out)
 
     // layout: per lattice two population copies and the density field
     const size_t rs = e->real_size();
-    std::vector<size_t> off_f0(n), off_f1(n), off_rho(n);
+    std::vector<size_t> off_f0(n), off_f1(n), off_r0(n), off_r1(n);
     size_t total = 0;
     for (int l = 0; l < n; ++l) {
         const size_t pitch = align_up((size_t)p[l].nx, 32), plane = pitch * p[l].ny;
@@ -469,7 +475,9 @@ int engine_create(const lb_params *p, int n, lb_engine **out)
         total = align_up(total + 18 * plane * rs, kAlign);
         off_f1[l] = total;
         total = align_up(total + 18 * plane * rs, kAlign);
-        off_rho[l] = total;
+        off_r0[l] = total;
+        total = align_up(total + 2 * plane * rs, kAlign);
+        off_r1[l] = total;
         total = align_up(total + 2 * plane * rs, kAlign);
     }
     if (cudaMalloc(&e->d_pool, total) != cudaSuccess) {
@@ -490,7 +498,8 @@ int engine_create(const lb_params *p, int n, lb_engine **out)
             fill_lat(L, p[l]);
             L.f[0] = (double *)(base + off_f0[l]);
             L.f[1] = (double *)(base + off_f1[l]);
-            L.rho = (double *)(base + off_rho[l]);
+            L.rho[0] = (double *)(base + off_r0[l]);
+            L.rho[1] = (double *)(base + off_r1[l]);
             L.tile_begin = begin;
             L.tile_end = end;
             e->L64.push_back(L);
@@ -499,7 +508,8 @@ int engine_create(const lb_params *p, int n, lb_engine **out)
             fill_lat(L, p[l]);
             L.f[0] = (float *)(base + off_f0[l]);
             L.f[1] = (float *)(base + off_f1[l]);
-            L.rho = (float *)(base + off_rho[l]);
+            L.rho[0] = (float *)(base + off_r0[l]);
+            L.rho[1] = (float *)(base + off_r1[l]);
             L.tile_begin = begin;
             L.tile_end = end;
             e->L32.push_back(L);
@@ -639,7 +649,7 @@ int lb_save(lb_handle *h, void *buf, size_t *len)
     CHECK_H(h);
     if (!len) return fail(LB_EINVAL, "len is NULL");
     lb_engine *e = h->e;
-    const size_t bytes = 18 * e->plane(0) * e->real_size();
+    const size_t bytes = e->pop_bytes(0) + e->ref_bytes(0);
     const size_t need = sizeof(SaveHeader) + bytes;
     if (!buf) {
         *len = need;
@@ -657,7 +667,11 @@ int lb_save(lb_handle *h, void *buf, size_t *len)
     std::memcpy(buf, &hd, sizeof hd);
     int rc = e->begin();
     if (rc) return rc;
-    LB_CUDA(cudaMemcpyAsync((char *)buf + sizeof hd, e->fbuf(0, e->parity), bytes, cudaMemcpyDeviceToHost, e->stream));
+    LB_CUDA(cudaMemcpyAsync((char *)buf + sizeof hd, e->fbuf(0, e->parity), e->pop_bytes(0), cudaMemcpyDeviceToHost,
+                            e->stream));
+    if (e->ref_bytes(0))
+        LB_CUDA(cudaMemcpyAsync((char *)buf + sizeof hd + e->pop_bytes(0), e->rbuf(0, e->parity), e->ref_bytes(0),
+                                cudaMemcpyDeviceToHost, e->stream));
     LB_CUDA(cudaStreamSynchronize(e->stream));
     *len = need;
     return e->end();
@@ -670,14 +684,17 @@ int lb_load(lb_handle *h, const void *buf, size_t len)
     lb_engine *e = h->e;
     SaveHeader hd;
     std::memcpy(&hd, buf, sizeof hd);
-    const size_t bytes = 18 * e->plane(0) * e->real_size();
+    const size_t bytes = e->pop_bytes(0) + e->ref_bytes(0);
     if (std::memcmp(hd.magic, "LBGB300", 8) != 0 || hd.precision != e->precision || hd.nx != e->nx(0) ||
         hd.ny != e->ny(0) || (size_t)hd.bytes != bytes || len < sizeof hd + bytes)
         return fail(LB_EINVAL, "checkpoint does not match this lattice");
     int rc = e->begin();
     if (rc) return rc;
-    LB_CUDA(cudaMemcpyAsync(e->fbuf(0, e->parity), (const char *)buf + sizeof hd, bytes, cudaMemcpyHostToDevice,
-                            e->stream));
+    LB_CUDA(cudaMemcpyAsync(e->fbuf(0, e->parity), (const char *)buf + sizeof hd, e->pop_bytes(0),
+                            cudaMemcpyHostToDevice, e->stream));
+    if (e->ref_bytes(0))
+        LB_CUDA(cudaMemcpyAsync(e->rbuf(0, e->parity), (const char *)buf + sizeof hd + e->pop_bytes(0), e->ref_bytes(0),
+                                cudaMemcpyHostToDevice, e->stream));
     LB_CUDA(cudaStreamSynchronize(e->stream));
     e->t = hd.t;
     return e->end();

@@ -3,11 +3,15 @@
 // population format:
 //   real = double : plain populations f; this instantiation is compiled
 //                   without fused multiply-add and evaluates every sum in the
-//                   same order as the step's definition below, so it reproduces
-//                   a straightforward FP64 evaluation of the equations up to
-//                   the last bit of exp().
-//   real = float  : offset populations g = f - w_i rho_ref_k; rho_k = rho_ref_k
-//                   + sum_i g; FMA contraction allowed.
+//                   same order as a direct evaluation of the equations, so it
+//                   reproduces a plain FP64 evaluation up to the last bit of exp().
+//   real = float  : offset populations h_i = f_i - w_i R, R the node's density
+//                   at the previous step (kept in the other density copy), so
+//                   the stored numbers are the small deviations from the local
+//                   equilibrium at rest and keep their low-order digits.  The
+//                   stencil and momentum sums are formed from differences of
+//                   opposite neighbours, which keeps them exactly antisymmetric
+//                   under reflection even with fused multiply-add (no drift).
 //
 // One time step is two launches over a list of tiles (lattice, x0, y0):
 //   k_density : rho_k = sum_i f_k,i                           (Eq. 6)
@@ -34,6 +38,9 @@ constexpr int HALO = 2;          // reach of the D2Q25 stencil
 constexpr int SW = TX + 2 * HALO;
 constexpr int SH = TY + 2 * HALO;
 constexpr int kThreads = TX * TY;
+
+template <typename real>
+constexpr bool kOffset = sizeof(real) == 4;
 
 // ---- lattice tables (Sec. II A; Fig. 1; Sec. II B after Eq. 8) ------------
 // D2Q9 order: rest, (1,0), (0,1), (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1).
@@ -65,11 +72,12 @@ __device__ __forceinline__ int wrap_index(int a, int n)
     return a < 0 ? a + n : a;
 }
 
-// Stage rho_k and psi_k of the tile plus its halo into shared memory.
-// Periodic copies in x (and in y without walls); beyond a wall the ghost rows
-// are either mirrored from the fluid or set to the fixed wall densities.
+// Stage rho_k and psi_k of the tile plus its halo into shared memory from the
+// density copy `rho`.  Periodic copies in x (and in y without walls); beyond a
+// wall the ghost rows are either mirrored from the fluid or set to the fixed
+// wall densities.
 template <typename real>
-__device__ __forceinline__ void stage_tile(const Lat<real> &L, int x0, int y0,
+__device__ __forceinline__ void stage_tile(const Lat<real> &L, const real *__restrict__ rho, int x0, int y0,
                                            real (*srho)[SH][SW], real (*spsi)[SH][SW], int tid, int nthreads)
 {
     const int nx = L.nx, ny = L.ny;
@@ -95,8 +103,8 @@ __device__ __forceinline__ void stage_tile(const Lat<real> &L, int x0, int y0,
         }
         if (!fixed) {
             const size_t c = (size_t)gy * L.pitch + gx;
-            rA = L.rho[c];
-            rB = L.rho[L.plane + c];
+            rA = rho[c];
+            rB = rho[L.plane + c];
         }
         srho[0][sy][sx] = rA;
         srho[1][sy][sx] = rB;
@@ -105,31 +113,65 @@ __device__ __forceinline__ void stage_tile(const Lat<real> &L, int x0, int y0,
     }
 }
 
-// sum_{i=1..8} w_i s(x + e_i) e_i, added in direction order (Eqs. 8, 9).
+// sum_{i=1..8} w_i s(x + e_i) e_i (Eqs. 8, 9).
+// FP64: added in direction order.  FP32: differences of opposite neighbours.
 template <typename real>
 __device__ __forceinline__ void q9_sum(const real (*s)[SW], int cx, int cy, real &sx, real &sy)
 {
     const real W1 = (real)(1.0 / 9.0), W2 = (real)(1.0 / 36.0);
-    const real a1 = W1 * s[cy][cx + 1], a2 = W1 * s[cy + 1][cx], a3 = W1 * s[cy][cx - 1], a4 = W1 * s[cy - 1][cx];
-    const real a5 = W2 * s[cy + 1][cx + 1], a6 = W2 * s[cy + 1][cx - 1];
-    const real a7 = W2 * s[cy - 1][cx - 1], a8 = W2 * s[cy - 1][cx + 1];
-    sx = ((((a1 - a3) + a5) - a6) - a7) + a8;
-    sy = ((((a2 - a4) + a5) + a6) - a7) - a8;
+    if constexpr (!kOffset<real>) {
+        const real a1 = W1 * s[cy][cx + 1], a2 = W1 * s[cy + 1][cx], a3 = W1 * s[cy][cx - 1], a4 = W1 * s[cy - 1][cx];
+        const real a5 = W2 * s[cy + 1][cx + 1], a6 = W2 * s[cy + 1][cx - 1];
+        const real a7 = W2 * s[cy - 1][cx - 1], a8 = W2 * s[cy - 1][cx + 1];
+        sx = ((((a1 - a3) + a5) - a6) - a7) + a8;
+        sy = ((((a2 - a4) + a5) + a6) - a7) - a8;
+    } else {
+        const real dE = s[cy][cx + 1] - s[cy][cx - 1];
+        const real dN = s[cy + 1][cx] - s[cy - 1][cx];
+        const real d1 = s[cy + 1][cx + 1] - s[cy - 1][cx - 1];   // (1,1) - (-1,-1)
+        const real d2 = s[cy - 1][cx + 1] - s[cy + 1][cx - 1];   // (1,-1) - (-1,1)
+        sx = W1 * dE + W2 * (d1 + d2);
+        sy = W1 * dN + W2 * (d1 - d2);
+    }
 }
 
-// sum_{j} p_j s(x + e_j) e_j over D2Q25 in raster order (dy outer, dx inner).
+// sum_j p_j s(x + e_j) e_j over D2Q25.
+// FP64: raster order (dy outer, dx inner).  FP32: opposite-neighbour
+// differences grouped by |e_x|, |e_y| class.
 template <typename real>
 __device__ __forceinline__ void q25_sum(const real (*s)[SW], int cx, int cy, real &sx, real &sy)
 {
-    sx = (real)0;
-    sy = (real)0;
+    if constexpr (!kOffset<real>) {
+        sx = (real)0;
+        sy = (real)0;
 #pragma unroll
-    for (int j = 0; j < 25; ++j) {
-        const int dx = j % 5 - 2, dy = j / 5 - 2;
-        if (dx == 0 && dy == 0) continue;
-        const real pp = (real)p25(dx * dx + dy * dy) * s[cy + dy][cx + dx];
-        if (dx != 0) sx += pp * (real)dx;
-        if (dy != 0) sy += pp * (real)dy;
+        for (int j = 0; j < 25; ++j) {
+            const int dx = j % 5 - 2, dy = j / 5 - 2;
+            if (dx == 0 && dy == 0) continue;
+            const real pp = (real)p25(dx * dx + dy * dy) * s[cy + dy][cx + dx];
+            if (dx != 0) sx += pp * (real)dx;
+            if (dy != 0) sy += pp * (real)dy;
+        }
+    } else {
+        real ax = (real)0, ay = (real)0;
+#pragma unroll
+        for (int a = 1; a <= 2; ++a) {   // axis classes (a,0) and (0,a)
+            const real p = (real)(p25(a * a) * a);
+            ax += p * (s[cy][cx + a] - s[cy][cx - a]);
+            ay += p * (s[cy + a][cx] - s[cy - a][cx]);
+        }
+#pragma unroll
+        for (int a = 1; a <= 2; ++a)
+#pragma unroll
+            for (int b = 1; b <= 2; ++b) {   // off-axis classes (a,b)
+                const real d1 = s[cy + b][cx + a] - s[cy - b][cx - a];   // (a,b) - (-a,-b)
+                const real d2 = s[cy - b][cx + a] - s[cy + b][cx - a];   // (a,-b) - (-a,b)
+                const real p = (real)p25(a * a + b * b);
+                ax += (p * (real)a) * (d1 + d2);
+                ay += (p * (real)b) * (d1 - d2);
+            }
+        sx = ax;
+        sy = ay;
     }
 }
 
@@ -168,28 +210,31 @@ __device__ __forceinline__ real guo_comp(real u, real eu)
 }
 
 // BGK relaxation with Guo forcing for direction I of one species
-// (Eqs. 1, 2, 5).  FP64: plain population; FP32: offset population with
-// delta = rho - rho_ref.
+// (Eqs. 1, 2, 5).  FP64: f -> f*.  FP32: the offset from the node's own
+// density, f - w rho -> f* - w rho (its equilibrium is w rho (e.u terms)).
 template <typename real, int I>
-__device__ __forceinline__ real collide_dir(real f, real rho, real delta, real ux, real uy, real uu,
-                                            real Fx, real Fy, real om, real aw)
+__device__ __forceinline__ real collide_dir(real f, real rho, real ux, real uy, real uu, real Fx, real Fy, real om,
+                                            real aw)
 {
     constexpr int EX = ex9(I), EY = ey9(I);
     const real w = (real)w9(I);
     const real eu = edot<real, EX, EY>(ux, uy);
     const real C = aw * (guo_comp<real, EX>(ux, eu) * Fx + guo_comp<real, EY>(uy, eu) * Fy);
-    if constexpr (sizeof(real) == 8) {
-        (void)delta;
+    if constexpr (!kOffset<real>) {
         const real feq = w * rho * ((real)1 + (real)3 * eu + (real)4.5 * eu * eu - (real)1.5 * uu);
         return f - om * (f - feq) + C;
     } else {
-        const real geq = w * (delta + rho * ((real)3 * eu + (real)4.5 * eu * eu - (real)1.5 * uu));
+        const real geq = (w * rho) * ((real)3 * eu + (real)4.5 * eu * eu - (real)1.5 * uu);
         return f - om * (f - geq) + C;
     }
 }
 
+// Store the post-collision value of direction I of species k at x + e_i
+// (half-way bounce-back: back to x, reversed).  FP32: re-reference the offset
+// from rho(x) to rho(x + e_i), the reference the next step reads there.
 template <typename real, int I>
-__device__ __forceinline__ void push_dir(const Lat<real> &L, real *__restrict__ fn, int k, int x, int y, real v)
+__device__ __forceinline__ void push_dir(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SH][SW], int k,
+                                         int x, int y, int cx, int cy, real v)
 {
     constexpr int EX = ex9(I), EY = ey9(I);
     int xd = x + EX, yd = y + EY;
@@ -198,50 +243,68 @@ __device__ __forceinline__ void push_dir(const Lat<real> &L, real *__restrict__ 
         if (xd < 0) xd += L.nx;
     }
     int dir = I;
+    bool reflect = false;
     if constexpr (EY != 0) {
         if (yd < 0 || yd >= L.ny) {
-            if (L.walls) {       // half-way bounce-back: back to this node, reversed
+            if (L.walls) {       // half-way bounce-back
                 dir = opp9(I);
                 xd = x;
                 yd = y;
+                reflect = true;
             } else {
                 yd = yd < 0 ? yd + L.ny : yd - L.ny;
             }
         }
     }
+    if constexpr (kOffset<real> && I != 0) {
+        if (!reflect) v += (real)w9(I) * (srho[k][cy][cx] - srho[k][cy + EY][cx + EX]);
+    }
+    (void)reflect;
     fn[(size_t)(k * 9 + dir) * L.plane + (size_t)yd * L.pitch + xd] = v;
 }
 
 template <typename real, int I>
-__device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__restrict__ fn, const real (&fk)[2][9],
-                                                 const real (&rho)[2], const real (&delta)[2], real ux, real uy, real uu,
-                                                 const real (&F)[2][2], int x, int y)
+__device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SH][SW],
+                                                 const real (&fk)[2][9], const real (&rho)[2], real ux, real uy, real uu,
+                                                 const real (&F)[2][2], int x, int y, int cx, int cy)
 {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const real v = collide_dir<real, I>(fk[k][I], rho[k], delta[k], ux, uy, uu, F[k][0], F[k][1], L.omega[k],
+        const real v = collide_dir<real, I>(fk[k][I], rho[k], ux, uy, uu, F[k][0], F[k][1], L.omega[k],
                                             L.aw[k][cls9(I)]);
-        push_dir<real, I>(L, fn, k, x, y, v);
+        push_dir<real, I>(L, fn, srho, k, x, y, cx, cy, v);
     }
 }
 
-// Species momentum sum_i f e_i in direction order, zero products dropped.
+// Species momentum sum_i f e_i.  FP64: direction order, zero products
+// dropped.  FP32: opposite-population differences.
 template <typename real>
 __device__ __forceinline__ void first_moment(const real (&f)[9], real &jx, real &jy)
 {
-    jx = ((((f[1] - f[3]) + f[5]) - f[6]) - f[7]) + f[8];
-    jy = ((((f[2] - f[4]) + f[5]) + f[6]) - f[7]) - f[8];
+    if constexpr (!kOffset<real>) {
+        jx = ((((f[1] - f[3]) + f[5]) - f[6]) - f[7]) + f[8];
+        jy = ((((f[2] - f[4]) + f[5]) + f[6]) - f[7]) - f[8];
+    } else {
+        const real d57 = f[5] - f[7], d86 = f[8] - f[6];
+        jx = (f[1] - f[3]) + (d57 + d86);
+        jy = (f[2] - f[4]) + (d57 - d86);
+    }
 }
 
 template <typename real>
 __device__ __forceinline__ real zeroth_moment(const real (&f)[9])
 {
-    return (((((((f[0] + f[1]) + f[2]) + f[3]) + f[4]) + f[5]) + f[6]) + f[7]) + f[8];
+    if constexpr (!kOffset<real>) {
+        return (((((((f[0] + f[1]) + f[2]) + f[3]) + f[4]) + f[5]) + f[6]) + f[7]) + f[8];
+    } else {
+        return f[0] + (((f[1] + f[3]) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8])));
+    }
 }
 
 // ---- kernels ----------------------------------------------------------------
 
-// rho_k = sum_i f_k,i (FP32: rho_ref_k + sum_i g_k,i).
+// rho_k = sum_i f_k,i into density copy parity^1 (FP32: R + sum_i h_i, R the
+// density of the previous step in copy parity).
 template <typename real>
 __global__ void __launch_bounds__(kThreads) k_density(const Lat<real> *__restrict__ lats, const int4 *__restrict__ tiles,
                                                       int tile_offset, int parity)
@@ -258,8 +321,8 @@ __global__ void __launch_bounds__(kThreads) k_density(const Lat<real> *__restric
 #pragma unroll
         for (int i = 0; i < 9; ++i) v[i] = f[(size_t)(k * 9 + i) * L.plane + c];
         real r = zeroth_moment<real>(v);
-        if constexpr (sizeof(real) == 4) r = L.rho_ref[k] + r;
-        L.rho[(size_t)k * L.plane + c] = r;
+        if constexpr (kOffset<real>) r = L.rho[parity][(size_t)k * L.plane + c] + r;
+        L.rho[parity ^ 1][(size_t)k * L.plane + c] = r;
     }
 }
 
@@ -273,7 +336,7 @@ __global__ void __launch_bounds__(kThreads) k_collide(const Lat<real> *__restric
     const int4 t = tiles[tile_offset + blockIdx.x];
     const Lat<real> &L = lats[t.x];
     const int tid = threadIdx.y * TX + threadIdx.x;
-    stage_tile<real>(L, t.y, t.z, srho, spsi, tid, kThreads);
+    stage_tile<real>(L, L.rho[parity ^ 1], t.y, t.z, srho, spsi, tid, kThreads);
     __syncthreads();
     const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
     if (x >= L.nx || y >= L.ny) return;
@@ -288,16 +351,21 @@ __global__ void __launch_bounds__(kThreads) k_collide(const Lat<real> *__restric
 #pragma unroll
         for (int i = 0; i < 9; ++i) fk[k][i] = fc[(size_t)(k * 9 + i) * L.plane + c];
 
-    real F[2][2], rho[2], delta[2], m[2][2];
+    real F[2][2], rho[2], m[2][2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         force_at<real>(L, srho, spsi, k, cx, cy, F[k][0], F[k][1]);
         rho[k] = srho[k][cy][cx];
-        delta[k] = (sizeof(real) == 4) ? zeroth_moment<real>(fk[k]) : (real)0;
         real jx, jy;
-        first_moment<real>(fk[k], jx, jy);
+        first_moment<real>(fk[k], jx, jy);     // FP32: the reference density adds no momentum
         m[k][0] = jx + (real)0.5 * F[k][0];   // Eq. (6), half force
         m[k][1] = jy + (real)0.5 * F[k][1];
+        if constexpr (kOffset<real>) {
+            // offsets from the node's current density: h_i - w_i (rho - R)
+            const real delta = zeroth_moment<real>(fk[k]);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fk[k][i] -= (real)w9(i) * delta;
+        }
     }
     // common velocity, Eq. (3)
     const real om0 = L.omega[0], om1 = L.omega[1];
@@ -306,15 +374,15 @@ __global__ void __launch_bounds__(kThreads) k_collide(const Lat<real> *__restric
     const real uy = (om0 * m[0][1] + om1 * m[1][1]) / den;
     const real uu = ux * ux + uy * uy;
 
-    collide_push_dir<real, 0>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
-    collide_push_dir<real, 1>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
-    collide_push_dir<real, 2>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
-    collide_push_dir<real, 3>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
-    collide_push_dir<real, 4>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
-    collide_push_dir<real, 5>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
-    collide_push_dir<real, 6>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
-    collide_push_dir<real, 7>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
-    collide_push_dir<real, 8>(L, fn, fk, rho, delta, ux, uy, uu, F, x, y);
+    collide_push_dir<real, 0>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+    collide_push_dir<real, 1>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+    collide_push_dir<real, 2>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+    collide_push_dir<real, 3>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+    collide_push_dir<real, 4>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+    collide_push_dir<real, 5>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+    collide_push_dir<real, 6>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+    collide_push_dir<real, 7>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+    collide_push_dir<real, 8>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
 }
 
 // ---- observables ------------------------------------------------------------
@@ -335,7 +403,8 @@ __device__ __forceinline__ double warp_max(double v)
 
 // Per-node diagnostics (densities, momenta with half force, barycentric
 // velocity, Eq. 11 bulk pressure) reduced per tile into FP64 partial sums;
-// optionally also written as dense FP64 fields [..][ny][nx].
+// optionally also written as dense FP64 fields [..][ny][nx].  Reads the
+// density copy parity^1 written by a density pass at the same time.
 template <typename real>
 __global__ void __launch_bounds__(kThreads) k_observe(const Lat<real> *__restrict__ lats, const int4 *__restrict__ tiles,
                                                       int tile_offset, int parity, double *__restrict__ partials,
@@ -348,7 +417,7 @@ __global__ void __launch_bounds__(kThreads) k_observe(const Lat<real> *__restric
     const int4 t = tiles[tile_offset + blockIdx.x];
     const Lat<real> &L = lats[t.x];
     const int tid = threadIdx.y * TX + threadIdx.x;
-    stage_tile<real>(L, t.y, t.z, srho, spsi, tid, kThreads);
+    stage_tile<real>(L, L.rho[parity ^ 1], t.y, t.z, srho, spsi, tid, kThreads);
     __syncthreads();
     const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
     double acc[kNumAcc];
@@ -366,7 +435,7 @@ __global__ void __launch_bounds__(kThreads) k_observe(const Lat<real> *__restric
             for (int i = 0; i < 9; ++i) fk[i] = fc[(size_t)(k * 9 + i) * L.plane + c];
             real Fx, Fy, jx, jy;
             force_at<real>(L, srho, spsi, k, cx, cy, Fx, Fy);
-            first_moment<real>(fk, jx, jy);
+            first_moment<real>(fk, jx, jy);   // FP32: the reference density adds no momentum
             r[k] = (double)srho[k][cy][cx];
             m[k][0] = (double)(jx + (real)0.5 * Fx);
             m[k][1] = (double)(jy + (real)0.5 * Fy);
@@ -487,8 +556,8 @@ __global__ void __launch_bounds__(256) k_finalize(const Lat<real> *__restrict__ 
 
 // ---- initialisation and population transfer ---------------------------------
 
-// f_k,i = f^eq_i(rho_k, u) (Eq. 2) from dense FP64 fields; FP32 stores the
-// offset f^eq - w_i rho_ref_k.
+// f_k,i = f^eq_i(rho_k, u) (Eq. 2) from dense FP64 fields.  FP32 stores the
+// reference R = rho (rounded) in density copy `parity` and h = f^eq - w R.
 template <typename real>
 __global__ void k_init(const Lat<real> *__restrict__ lats, int lat, const double *__restrict__ rho,
                        const double *__restrict__ u, int parity)
@@ -503,16 +572,22 @@ __global__ void k_init(const Lat<real> *__restrict__ lats, int lat, const double
     const size_t c = (size_t)y * L.pitch + x;
     for (int k = 0; k < 2; ++k) {
         const double r = rho[k * n + d];
+        double R = 0.0;
+        if constexpr (kOffset<real>) {
+            const real Rr = (real)r;
+            L.rho[parity][(size_t)k * L.plane + c] = Rr;
+            R = (double)Rr;
+        }
         for (int i = 0; i < 9; ++i) {
             const double eu = ex9(i) * ux + ey9(i) * uy;
             const double feq = w9(i) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
-            f[(size_t)(k * 9 + i) * L.plane + c] = (real)(feq - w9(i) * (double)L.rho_ref[k]);
+            f[(size_t)(k * 9 + i) * L.plane + c] = (real)(feq - w9(i) * R);
         }
     }
 }
 
-// dense FP64 [2][9][ny][nx] <-> native pitched populations (offsets added back
-// or removed for FP32).
+// dense FP64 [2][9][ny][nx] <-> native pitched populations (FP32: the
+// reference density added back, or recomputed as sum_i f_i on input).
 template <typename real>
 __global__ void k_get_pops(const Lat<real> *__restrict__ lats, int lat, int parity, double *__restrict__ out)
 {
@@ -520,10 +595,11 @@ __global__ void k_get_pops(const Lat<real> *__restrict__ lats, int lat, int pari
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= L.nx || y >= L.ny) return;
     const size_t n = (size_t)L.nx * L.ny, d = (size_t)y * L.nx + x, c = (size_t)y * L.pitch + x;
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k) {
+        const double R = kOffset<real> ? (double)L.rho[parity][(size_t)k * L.plane + c] : 0.0;
         for (int i = 0; i < 9; ++i)
-            out[(size_t)(k * 9 + i) * n + d] =
-                (double)L.f[parity][(size_t)(k * 9 + i) * L.plane + c] + w9(i) * (double)L.rho_ref[k];
+            out[(size_t)(k * 9 + i) * n + d] = (double)L.f[parity][(size_t)(k * 9 + i) * L.plane + c] + w9(i) * R;
+    }
 }
 
 template <typename real>
@@ -533,10 +609,18 @@ __global__ void k_set_pops(const Lat<real> *__restrict__ lats, int lat, int pari
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= L.nx || y >= L.ny) return;
     const size_t n = (size_t)L.nx * L.ny, d = (size_t)y * L.nx + x, c = (size_t)y * L.pitch + x;
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k) {
+        double R = 0.0;
+        if constexpr (kOffset<real>) {
+            double s = 0.0;
+            for (int i = 0; i < 9; ++i) s += in[(size_t)(k * 9 + i) * n + d];
+            const real Rr = (real)s;
+            L.rho[parity][(size_t)k * L.plane + c] = Rr;
+            R = (double)Rr;
+        }
         for (int i = 0; i < 9; ++i)
-            L.f[parity][(size_t)(k * 9 + i) * L.plane + c] =
-                (real)(in[(size_t)(k * 9 + i) * n + d] - w9(i) * (double)L.rho_ref[k]);
+            L.f[parity][(size_t)(k * 9 + i) * L.plane + c] = (real)(in[(size_t)(k * 9 + i) * n + d] - w9(i) * R);
+    }
 }
 
 }  // namespace lbk

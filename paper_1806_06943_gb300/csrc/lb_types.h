@@ -3,7 +3,9 @@
 //
 // Memory layout in HBM (one lattice):
 //   populations  f[species][dir][y][pitch]   two ping-pong copies
-//   densities    rho[species][y][pitch]       written by the density pass
+//   densities    rho[species][y][pitch]       two copies: the density pass of
+//                                              a step with parity p writes copy
+//                                              p^1, the fused kernel reads it
 // pitch = nx rounded up to 32 elements, so every row starts on a 128-byte
 // (FP32) or 256-byte (FP64) boundary and a warp's row segment is one or two
 // full cache lines.  A batch of lattices shares one allocation; each lattice
@@ -32,7 +34,7 @@ constexpr int kObsStride = 16;
 template <typename real>
 struct Lat {
     real *f[2];          // ping-pong population buffers
-    real *rho;           // density pass output
+    real *rho[2];        // density of the previous step (FP32 reference) / of this step
     size_t plane;        // elements per [y][pitch] plane = ny * pitch
     int32_t nx, ny, pitch;
     int32_t walls;       // 0 periodic, 1 bounce-back walls in y
@@ -45,7 +47,6 @@ struct Lat {
     real G1, G2, GAB;
     real g[2];
     real wall_rho[2];
-    real rho_ref[2];     // offsets of the FP32 populations (0 for FP64)
     // observable settings, always FP64
     double probe[3];     // cx, cy, R
     double tau_B;        // for the closed-form flux Q0

@@ -40,7 +40,6 @@ class lb_params(ctypes.Structure):
         ("walls", ctypes.c_int32), ("wall_mode", ctypes.c_int32),
         ("wall_rho", ctypes.c_double * 2),
         ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
-        ("rho_ref", ctypes.c_double * 2),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -141,7 +140,7 @@ def _host_ptr(a: np.ndarray | None, shape, writable=False):
 
 
 def make_params(nx, ny, tau=(1.0, 1.0), G_AB=3.0, G1=-7.4, G2=6.4, g=(0.0, 0.0), walls=0, wall_mode=0,
-                wall_rho=(0.0, 0.0), precision=LB_FP64, rho_ref=(1.0, 1.0), stream=None) -> lb_params:
+                wall_rho=(0.0, 0.0), precision=LB_FP64, stream=None) -> lb_params:
     p = lb_params()
     p.nx, p.ny = int(nx), int(ny)
     p.tau[0], p.tau[1] = float(tau[0]), float(tau[1])
@@ -150,7 +149,6 @@ def make_params(nx, ny, tau=(1.0, 1.0), G_AB=3.0, G1=-7.4, G2=6.4, g=(0.0, 0.0),
     p.walls, p.wall_mode = int(walls), int(wall_mode)
     p.wall_rho[0], p.wall_rho[1] = float(wall_rho[0]), float(wall_rho[1])
     p.precision = int(precision)
-    p.rho_ref[0], p.rho_ref[1] = float(rho_ref[0]), float(rho_ref[1])
     p.stream = stream
     return p
 
@@ -265,7 +263,7 @@ class Batch:
         for i, s in enumerate(specs):
             kw = dict(common)
             kw.update({k: v for k, v in s.items() if k in (
-                "tau", "G_AB", "G1", "G2", "g", "walls", "wall_mode", "wall_rho", "precision", "rho_ref", "stream")})
+                "tau", "G_AB", "G1", "G2", "g", "walls", "wall_mode", "wall_rho", "precision", "stream")})
             arr[i] = make_params(s["nx"], s["ny"], **kw)
             self.shapes.append((int(s["ny"]), int(s["nx"])))
         self.params = arr

@@ -24,8 +24,8 @@ def test_every_declared_symbol_is_exported(lbmod):
 
 
 def test_struct_layouts_match_header(lbmod):
-    # lb_params: 2 ints, 2 doubles, 3 doubles, 2 doubles, 2 ints, 2 doubles, 2 ints, 2 doubles, pointer
-    assert ctypes.sizeof(lbmod.lb_params) == 8 + 16 + 24 + 16 + 8 + 16 + 8 + 16 + 8
+    # lb_params: 2 ints, 2 doubles, 3 doubles, 2 doubles, 2 ints, 2 doubles, 2 ints, pointer
+    assert ctypes.sizeof(lbmod.lb_params) == 8 + 16 + 24 + 16 + 8 + 16 + 8 + 8
     assert ctypes.sizeof(lbmod.lb_obs) == 8 + 16 + 32 + 8 * 5 + 8
 
 

@@ -26,17 +26,18 @@ def lbmod():
     return lb
 
 
-def nrel(a, b):
-    den = np.max(np.abs(b))
+def nrel(a, b, floor=0.0):
+    """||a - b||_inf / max(||b||_inf, floor)."""
+    den = max(np.max(np.abs(b)), floor)
     return np.max(np.abs(a - b)) / (den if den > 0 else 1.0)
 
 
-def run_pair(oracle_mod, lbmod, rho, steps, u=None, precision=0, rho_ref=(1.0, 1.0), probe=None, **kw):
+def run_pair(oracle_mod, lbmod, rho, steps, u=None, precision=0, probe=None, **kw):
     ny, nx = rho.shape[1:]
     o = oracle_mod.OracleSim(nx, ny, **kw)
     o.set_fields(rho, u)
     o.step(steps)
-    g = lbmod.Lattice(nx, ny, precision=precision, rho_ref=rho_ref, **kw)
+    g = lbmod.Lattice(nx, ny, precision=precision, **kw)
     g.set_fields(rho, u)
     g.step(steps)
     if probe is not None:
@@ -81,7 +82,9 @@ def test_fp64_parity_shapes(oracle_mod, lbmod, nx, ny, walls, wall_mode, tau, g)
     o, gl = run_pair(oracle_mod, lbmod, rho, 300, **kw)
     fo, fg = o.fields(), gl.fields()
     assert nrel(fg["rho"], fo["rho"]) <= 1e-12
-    assert nrel(fg["ubar"], fo["ubar"]) <= 1e-12
+    # the 5x5 drop dissolves and its velocities fall to ~1e-7: compare those
+    # against a velocity scale of 1e-3 instead of their own round-off size
+    assert nrel(fg["ubar"], fo["ubar"], floor=1e-3) <= 1e-12
     assert nrel(gl.get_populations(), o.get_f()) <= 1e-12
     oo, og = o.observables(), gl.observables()
     if walls and g[0] != 0.0:
@@ -101,7 +104,7 @@ def test_fp64_initial_velocity_and_single_step(oracle_mod, lbmod):
 def test_fp32_offset_c1_droplet(oracle_mod, lbmod):
     """FP32 offset populations against the FP64 oracle, 2000 steps."""
     rho = W.c1_droplet_64()
-    o, g = run_pair(oracle_mod, lbmod, rho, 2000, precision=1, rho_ref=(1.0, 1.0), **C6)
+    o, g = run_pair(oracle_mod, lbmod, rho, 2000, precision=1, **C6)
     fo, fg = o.fields(), g.fields()
     er, eu = nrel(fg["rho"], fo["rho"]), nrel(fg["ubar"], fo["ubar"])
     assert er <= 1e-5, er
@@ -195,7 +198,10 @@ def test_runs_are_deterministic(lbmod):
         a.set_probe(32, 24, 11)
         out.append((a.get_populations(), a.observables()))
     assert np.array_equal(out[0][0], out[1][0])
-    assert out[0][1] == out[1][1]
+    a, b = out[0][1], out[1][1]
+    assert a.keys() == b.keys()
+    for k in a:   # bitwise, NaN (no walls: mu_r) equal to NaN
+        assert (a[k] == b[k]) or (np.isnan(a[k]) and np.isnan(b[k])), k
 
 
 def test_unstable_run_reports_error_without_fault(lbmod):
