@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 C6 = dict(G_AB=3.0, G1=-7.4, G2=6.4)
 FLUSH_BYTES = 256 << 20
 BYTES_COLLIDE = {1: 152, 0: 304}   # algorithmic bytes / site: 18 pops read + 18 written + 2 rho read
-BYTES_DENSITY = {1: 80, 0: 160}    # 18 pops read + 2 rho written
+BYTES_DENSITY = {1: 88, 0: 160}    # 18 pops read + 2 rho written (+ 2 reference rho read in FP32)
 
 
 def parse():
@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--quick", action="store_true", help="main leg only")
+    ap.add_argument("--workload", default="laplace_sweep_24",
+                    choices=["laplace_sweep_24", "dense_emulsion_4096", "dense_emulsion_2048"],
+                    help="main-leg workload (the dense emulsions are single periodic lattices)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     return ap.parse_args()
 
 
@@ -100,12 +104,21 @@ def sweep_fields():
     return specs, fields
 
 
+def dense_emulsion(n):
+    """n x n periodic emulsion, radii U[8, 20], target area fraction 0.6,
+    dispersed/continuous viscosity ratio 5 (tau_d = 3, tau_c = 1)."""
+    from paper_1806_06943_gb300 import workloads as W
+    rho, _, radii, phi = W.random_emulsion(n, n, 0.6, 8.0, 20.0, seed=W.BASE_SEED + 4)
+    return [dict(nx=n, ny=n, tau=(3.0, 1.0), R=0.0)], [rho], {"phi_achieved": phi, "droplets": len(radii)}
+
+
 def make_batch(lb, specs, fields, precision, stream):
     b = lb.Batch([dict(nx=s["nx"], ny=s["ny"], tau=s["tau"]) for s in specs], precision=precision,
                  stream=stream, **C6)
     for i, (s, r) in enumerate(zip(specs, fields)):
         b.set_fields(i, r)
-        b.set_probe(i, s["nx"] / 2, s["ny"] / 2, s["R"])
+        if s.get("R", 0.0) > 0.0:
+            b.set_probe(i, s["nx"] / 2, s["ny"] / 2, s["R"])
     return b
 
 
@@ -257,9 +270,14 @@ def main():
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     peak, peak_kind = measured_peaks()
 
-    specs, fields = sweep_fields()
+    extra_cfg = {}
+    if args.workload == "laplace_sweep_24":
+        specs, fields = sweep_fields()
+    else:
+        specs, fields, extra_cfg = dense_emulsion(int(args.workload.rsplit("_", 1)[1]))
     sites = sum(s["nx"] * s["ny"] for s in specs)
-    b = make_batch(lb, specs, fields, lb.LB_FP32, sptr)
+    prec = lb.LB_FP32 if args.precision == "fp32" else lb.LB_FP64
+    b = make_batch(lb, specs, fields, prec, sptr)
 
     # warm-up (untimed), then the timed region: K steps, barrier + sync on both sides
     b.profile(args.warmup, flush.data_ptr(), FLUSH_BYTES)
@@ -285,31 +303,35 @@ def main():
     out = {
         "metric": "2-species MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == lb.LB_FP32 else "f64",
         "data": "synthetic",
-        "config": {"workload": "laplace_sweep_24", "lattices": len(specs), "sites": sites,
-                   "sizes": "128^2..384^2, R 10..45, mu_d/mu_c 1, 3, 10 (tau_c = 1)",
-                   "precision": "fp32 offset populations (per-node reference density), fp64 reductions",
+        "config": {"workload": args.workload, "lattices": len(specs), "sites": sites,
+                   "sizes": ("128^2..384^2, R 10..45, mu_d/mu_c 1, 3, 10 (tau_c = 1)"
+                             if args.workload == "laplace_sweep_24" else
+                             "periodic emulsion, R U[8,20], phi 0.6, mu_d/mu_c 5"), **extra_cfg,
+                   "precision": ("fp32 offset populations (per-node reference density), fp64 reductions"
+                                 if prec == lb.LB_FP32 else "fp64 populations"),
                    "couplings": C6, "l2": "flushed (256 MiB write) before every timed step",
                    "timing": "CUDA events per kernel on the launching stream", "parallelism": f"replicas x{world}"},
         "clocks": clk,
         "gpu_launches": gpu_launches,
         "roofline": {
-            "bound": "hbm", "kernel": "k_collide<float> (fused force+collide+stream)",
-            "achieved": BYTES_COLLIDE[1] * sites / (ms[1] * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-            "frac": BYTES_COLLIDE[1] * sites / (ms[1] * 1e-3) / 1e9 / peak, "traffic": None,
+            "bound": "hbm", "kernel": f"k_collide<{'float' if prec else 'double'}> (fused force+collide+stream)",
+            "achieved": BYTES_COLLIDE[prec] * sites / (ms[1] * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": BYTES_COLLIDE[prec] * sites / (ms[1] * 1e-3) / 1e9 / peak, "traffic": None,
             "peak_source": f"{peak_kind} hbm_gbs (burst)",
-            "algorithmic_bytes_per_site": BYTES_COLLIDE[1], "units_per_launch": sites,
+            "algorithmic_bytes_per_site": BYTES_COLLIDE[prec], "units_per_launch": sites,
             "ms_per_launch": ms[1],
         },
-        "density_pass": {"ms_per_launch": ms[0], "algorithmic_bytes_per_site": BYTES_DENSITY[1],
-                         "achieved_gbs": BYTES_DENSITY[1] * sites / (ms[0] * 1e-3) / 1e9},
+        "density_pass": {"ms_per_launch": ms[0], "algorithmic_bytes_per_site": BYTES_DENSITY[prec],
+                         "achieved_gbs": BYTES_DENSITY[prec] * sites / (ms[0] * 1e-3) / 1e9},
         "wall_s_timed": t_wall,
         "observables_after": {"finite": all(o["finite"] == 1.0 for o in obs),
                               "gamma_fit_ratio1": None},
     }
 
-    if not args.quick:
+    if not args.quick and args.workload == "laplace_sweep_24" and prec == lb.LB_FP32:
         # sustained rate through the public step call (CUDA graphs, no flush)
         b.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -42,6 +42,12 @@ constexpr int kThreads = TX * TY;
 template <typename real>
 constexpr bool kOffset = sizeof(real) == 4;
 
+// Resident blocks per SM the fused kernel is compiled for: the FP32 kernel is
+// bound by HBM and needs the warps to keep enough loads in flight; the FP64
+// kernel is bound by the FP64 pipe and keeps its registers.
+template <typename real>
+constexpr int kCollideMinBlocks = kOffset<real> ? 4 : 2;
+
 // ---- lattice tables (Sec. II A; Fig. 1; Sec. II B after Eq. 8) ------------
 // D2Q9 order: rest, (1,0), (0,1), (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1).
 __host__ __device__ constexpr int ex9(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
@@ -81,6 +87,21 @@ __device__ __forceinline__ void stage_tile(const Lat<real> &L, const real *__res
                                            real (*srho)[SH][SW], real (*spsi)[SH][SW], int tid, int nthreads)
 {
     const int nx = L.nx, ny = L.ny;
+    // tiles whose halo lies inside the lattice need no wrapping or ghosts
+    const bool inner = x0 >= HALO && x0 + TX + HALO <= nx && y0 >= HALO && y0 + TY + HALO <= ny;
+    if (inner) {
+        const real *__restrict__ base = rho + (size_t)(y0 - HALO) * L.pitch + (x0 - HALO);
+        for (int idx = tid; idx < SW * SH; idx += nthreads) {
+            const int sx = idx % SW, sy = idx / SW;
+            const size_t c = (size_t)sy * L.pitch + sx;
+            const real rA = base[c], rB = base[L.plane + c];
+            srho[0][sy][sx] = rA;
+            srho[1][sy][sx] = rB;
+            spsi[0][sy][sx] = psi_of<real>(rA);
+            spsi[1][sy][sx] = psi_of<real>(rB);
+        }
+        return;
+    }
     for (int idx = tid; idx < SW * SH; idx += nthreads) {
         const int sx = idx % SW, sy = idx / SW;
         const int gx = wrap_index(x0 + sx - HALO, nx);
@@ -232,47 +253,81 @@ __device__ __forceinline__ real collide_dir(real f, real rho, real ux, real uy, 
 // Store the post-collision value of direction I of species k at x + e_i
 // (half-way bounce-back: back to x, reversed).  FP32: re-reference the offset
 // from rho(x) to rho(x + e_i), the reference the next step reads there.
-template <typename real, int I>
+template <typename real, int I, bool kInner>
 __device__ __forceinline__ void push_dir(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SH][SW], int k,
                                          int x, int y, int cx, int cy, real v)
 {
     constexpr int EX = ex9(I), EY = ey9(I);
-    int xd = x + EX, yd = y + EY;
-    if constexpr (EX != 0) {
-        if (xd >= L.nx) xd -= L.nx;
-        if (xd < 0) xd += L.nx;
+    if constexpr (kOffset<real> && I != 0) {
+        // the next step's reference at the destination is its density now
+        if (kInner || !(EY != 0 && L.walls && (y + EY < 0 || y + EY >= L.ny)))
+            v += (real)w9(I) * (srho[k][cy][cx] - srho[k][cy + EY][cx + EX]);
     }
-    int dir = I;
-    bool reflect = false;
-    if constexpr (EY != 0) {
-        if (yd < 0 || yd >= L.ny) {
-            if (L.walls) {       // half-way bounce-back
-                dir = opp9(I);
-                xd = x;
-                yd = y;
-                reflect = true;
-            } else {
-                yd = yd < 0 ? yd + L.ny : yd - L.ny;
+    if constexpr (kInner) {
+        // node and destination inside the lattice: a constant offset
+        fn[(size_t)(k * 9 + I) * L.plane + ((size_t)y * L.pitch + x) + (EY * L.pitch + EX)] = v;
+        return;
+    } else {
+        int xd = x + EX, yd = y + EY;
+        if constexpr (EX != 0) {
+            if (xd >= L.nx) xd -= L.nx;
+            if (xd < 0) xd += L.nx;
+        }
+        int dir = I;
+        if constexpr (EY != 0) {
+            if (yd < 0 || yd >= L.ny) {
+                if (L.walls) {       // half-way bounce-back: back to this node, reversed
+                    dir = opp9(I);
+                    xd = x;
+                    yd = y;
+                } else {
+                    yd = yd < 0 ? yd + L.ny : yd - L.ny;
+                }
             }
         }
+        fn[(size_t)(k * 9 + dir) * L.plane + (size_t)yd * L.pitch + xd] = v;
     }
-    if constexpr (kOffset<real> && I != 0) {
-        if (!reflect) v += (real)w9(I) * (srho[k][cy][cx] - srho[k][cy + EY][cx + EX]);
-    }
-    (void)reflect;
-    fn[(size_t)(k * 9 + dir) * L.plane + (size_t)yd * L.pitch + xd] = v;
 }
 
-template <typename real, int I>
+// FP32 per-species constants of the collision shared by all directions.
+template <typename real>
+struct SpeciesTerms {
+    real uF[2];        // u^eq . F_k
+    real wr[2][3];     // w(|e|^2) rho_k
+    real aw3[2][3];    // 3 (1 - omega_k/2) w(|e|^2)
+};
+
+template <typename real, int I, bool kInner>
 __device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SH][SW],
                                                  const real (&fk)[2][9], const real (&rho)[2], real ux, real uy, real uu,
-                                                 const real (&F)[2][2], int x, int y, int cx, int cy)
+                                                 const real (&F)[2][2], const SpeciesTerms<real> &st, int x, int y,
+                                                 int cx, int cy)
 {
+    if constexpr (!kOffset<real>) {
+        (void)st;
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const real v = collide_dir<real, I>(fk[k][I], rho[k], ux, uy, uu, F[k][0], F[k][1], L.omega[k],
-                                            L.aw[k][cls9(I)]);
-        push_dir<real, I>(L, fn, srho, k, x, y, cx, cy, v);
+        for (int k = 0; k < 2; ++k) {
+            const real v = collide_dir<real, I>(fk[k][I], rho[k], ux, uy, uu, F[k][0], F[k][1], L.omega[k],
+                                                L.aw[k][cls9(I)]);
+            push_dir<real, I, kInner>(L, fn, srho, k, x, y, cx, cy, v);
+        }
+    } else {
+        // Eq. (2) less w rho (the node's own density is the offset), and Eq. (5)
+        // rewritten as 3 (1 - 1/2tau) w [(e.F)(1 + 3 e.u) - u.F]; the direction
+        // terms are shared by both species.
+        constexpr int EX = ex9(I), EY = ey9(I), C = cls9(I);
+        const real eu = edot<real, EX, EY>(ux, uy);
+        const real q = (real)4.5 * eu * eu + ((real)3 * eu - (real)1.5 * uu);
+        const real tt = (real)1 + (real)3 * eu;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const real eF = edot<real, EX, EY>(F[k][0], F[k][1]);
+            const real Cg = st.aw3[k][C] * (eF * tt - st.uF[k]);
+            const real geq = st.wr[k][C] * q;
+            const real f = fk[k][I];
+            const real v = (f + L.omega[k] * (geq - f)) + Cg;
+            push_dir<real, I, kInner>(L, fn, srho, k, x, y, cx, cy, v);
+        }
     }
 }
 
@@ -326,31 +381,50 @@ __global__ void __launch_bounds__(kThreads) k_density(const Lat<real> *__restric
     }
 }
 
+template <typename real, bool kInner>
+__device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SH][SW],
+                                             const real (*spsi)[SH][SW], real (&fk)[2][9], int x, int y, int cx, int cy);
+
 // Fused force + collision + push-streaming + bounce-back for one tile.
 template <typename real>
-__global__ void __launch_bounds__(kThreads) k_collide(const Lat<real> *__restrict__ lats, const int4 *__restrict__ tiles,
+__global__ void __launch_bounds__(kThreads, kCollideMinBlocks<real>) k_collide(const Lat<real> *__restrict__ lats, const int4 *__restrict__ tiles,
                                                       int tile_offset, int parity)
 {
     __shared__ real srho[2][SH][SW];
     __shared__ real spsi[2][SH][SW];
+    __shared__ Lat<real> sL;   // descriptor copy: stores to fn cannot alias it
     const int4 t = tiles[tile_offset + blockIdx.x];
-    const Lat<real> &L = lats[t.x];
+    const Lat<real> &G = lats[t.x];
     const int tid = threadIdx.y * TX + threadIdx.x;
-    stage_tile<real>(L, L.rho[parity ^ 1], t.y, t.z, srho, spsi, tid, kThreads);
-    __syncthreads();
+    static_assert(sizeof(Lat<real>) % 4 == 0, "descriptor copied as 32-bit words");
+    if (tid < (int)(sizeof(Lat<real>) / 4))
+        reinterpret_cast<uint32_t *>(&sL)[tid] = reinterpret_cast<const uint32_t *>(&G)[tid];
     const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
-    if (x >= L.nx || y >= L.ny) return;
-    const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
-
+    const bool valid = x < G.nx && y < G.ny;
+    const Lat<real> &L = G;
+    // issue the population loads first so their latency overlaps the staging
     const real *__restrict__ fc = L.f[parity];
     real *__restrict__ fn = L.f[parity ^ 1];
-    const size_t c = (size_t)y * L.pitch + x;
+    const size_t c = valid ? (size_t)y * L.pitch + x : 0;
     real fk[2][9];
 #pragma unroll
     for (int k = 0; k < 2; ++k)
 #pragma unroll
-        for (int i = 0; i < 9; ++i) fk[k][i] = fc[(size_t)(k * 9 + i) * L.plane + c];
+        for (int i = 0; i < 9; ++i) fk[k][i] = valid ? fc[(size_t)(k * 9 + i) * L.plane + c] : (real)0;
+    stage_tile<real>(L, L.rho[parity ^ 1], t.y, t.z, srho, spsi, tid, kThreads);
+    __syncthreads();
+    if (!valid) return;
+    const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
+    // tiles whose pushes stay inside the lattice (no wrap, no wall) take constant offsets
+    const bool inner = t.y >= 1 && t.y + TX + 1 <= sL.nx && t.z >= 1 && t.z + TY + 1 <= sL.ny;
+    if (inner) collide_site<real, true>(sL, fn, srho, spsi, fk, x, y, cx, cy);
+    else collide_site<real, false>(sL, fn, srho, spsi, fk, x, y, cx, cy);
+}
 
+template <typename real, bool kInner>
+__device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SH][SW],
+                                             const real (*spsi)[SH][SW], real (&fk)[2][9], int x, int y, int cx, int cy)
+{
     real F[2][2], rho[2], m[2][2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -373,16 +447,28 @@ __global__ void __launch_bounds__(kThreads) k_collide(const Lat<real> *__restric
     const real ux = (om0 * m[0][0] + om1 * m[1][0]) / den;
     const real uy = (om0 * m[0][1] + om1 * m[1][1]) / den;
     const real uu = ux * ux + uy * uy;
+    SpeciesTerms<real> st;
+    if constexpr (kOffset<real>) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            st.uF[k] = ux * F[k][0] + uy * F[k][1];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                st.wr[k][c] = (real)w9(c == 0 ? 0 : (c == 1 ? 1 : 5)) * rho[k];
+                st.aw3[k][c] = (real)3 * L.aw[k][c];
+            }
+        }
+    }
 
-    collide_push_dir<real, 0>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
-    collide_push_dir<real, 1>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
-    collide_push_dir<real, 2>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
-    collide_push_dir<real, 3>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
-    collide_push_dir<real, 4>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
-    collide_push_dir<real, 5>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
-    collide_push_dir<real, 6>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
-    collide_push_dir<real, 7>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
-    collide_push_dir<real, 8>(L, fn, srho, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+    collide_push_dir<real, 0, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 1, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 2, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 3, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 4, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 5, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 6, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 7, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 8, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
 }
 
 // ---- observables ------------------------------------------------------------
