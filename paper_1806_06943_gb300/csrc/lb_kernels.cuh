@@ -33,7 +33,7 @@
 namespace lbk {
 
 constexpr int TX = 32;           // tile width = threads in x
-constexpr int TY = 8;            // tile height = threads in y
+constexpr int TY = 4;            // tile height = threads in y
 constexpr int HALO = 2;          // reach of the D2Q25 stencil
 constexpr int SW = TX + 2 * HALO;
 constexpr int SH = TY + 2 * HALO;
@@ -46,7 +46,7 @@ constexpr bool kOffset = sizeof(real) == 4;
 // bound by HBM and needs the warps to keep enough loads in flight; the FP64
 // kernel is bound by the FP64 pipe and keeps its registers.
 template <typename real>
-constexpr int kCollideMinBlocks = kOffset<real> ? 4 : 2;
+constexpr int kCollideMinBlocks = kOffset<real> ? 8 : 4;
 
 // ---- lattice tables (Sec. II A; Fig. 1; Sec. II B after Eq. 8) ------------
 // D2Q9 order: rest, (1,0), (0,1), (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1).
