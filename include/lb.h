@@ -216,6 +216,39 @@ int lb_batch_get_fields(lb_batch *b, int32_t i, double *rho, double *mom, double
 /* As lb_profile, over all lattices of the batch (one launch covers them all). */
 int lb_batch_profile(lb_batch *b, int32_t nsteps, void *flush_buf, size_t flush_bytes, double ms[3]);
 
+/* ---- observables without any allocation ------------------------------------ */
+
+/* Largest lattice lb_observables_static accepts, in tiles of 32 x 4 nodes
+ * (32768 tiles: 4,194,304 nodes, e.g. 2048 x 2048). */
+#define LB_STATIC_MAX_TILES 32768
+
+/* Observables of an LB_FP64 lattice whose populations live in the caller's
+ * device memory, computed without allocating memory of any kind.  No
+ * counterpart in the paper: this is a service for callers that may not call
+ * cudaMalloc (or anything that allocates) once they run, e.g. an application
+ * that owns a fixed device-memory budget or a solver step that must not enter
+ * the driver's allocator.
+ *   p     lattice parameters (precision must be LB_FP64; p->stream is the
+ *         stream the two kernels are launched on, NULL for the default stream)
+ *   f     device [2][9][ny][nx] FP64 populations, direction order as for
+ *         lb_get_populations
+ *   cx, cy, R   Laplace probe as for lb_set_probe (R <= 0: none)
+ *   obs   device array of 16 doubles receiving, in order: mass A, mass B,
+ *         momentum A (x, y), momentum B (x, y), flux_Q, mu_r, dp_laplace,
+ *         R_eff, umax, finite (1.0 or 0.0), then four zeros; the definitions
+ *         are those of lb_obs
+ * The scratch is a file-scope device array of LB_STATIC_MAX_TILES x 16
+ * doubles (4 MiB) that every GPU which loads the library holds until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (once per device, with that device current), so make the first
+ * call before any stream capture.  Every call shares the array and leaves
+ * its contents behind; calls whose kernels overlap on the GPU race on it, so
+ * serialise them (one stream, or events).  Asynchronous: obs is written when
+ * the stream reaches the kernels.  Returns LB_EINVAL for NULL pointers, a
+ * precision other than LB_FP64, invalid sizes or parameters, or a lattice of
+ * more than LB_STATIC_MAX_TILES tiles; LB_ECUDA if a launch fails. */
+int lb_observables_static(const lb_params *p, const double *f, double cx, double cy, double R, double *obs);
+
 #ifdef __cplusplus
 }
 #endif

@@ -542,6 +542,10 @@ struct SaveHeader {
 
 }  // namespace
 
+namespace lbk {
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace lbk
+
 struct lb_handle {
     lb_engine *e;
 };

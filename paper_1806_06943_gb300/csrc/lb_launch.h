@@ -29,4 +29,7 @@ struct Launch {
 extern template struct Launch<double>;
 extern template struct Launch<float>;
 
+// Record msg as the calling thread's lb_last_error() message.
+void set_last_error(const char *msg);
+
 }  // namespace lbk

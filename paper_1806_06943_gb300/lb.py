@@ -23,6 +23,7 @@ LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_ETIMEOUT = 0, -1, -2, -3
 LB_FP64, LB_FP32 = 0, 1
 LB_PERIODIC, LB_WALLS_Y = 0, 1
 LB_WALL_MIRROR, LB_WALL_FIXED = 0, 1
+LB_STATIC_MAX_TILES = 32768
 
 
 class LBError(RuntimeError):
@@ -98,6 +99,7 @@ SIGNATURES = {
     "lb_batch_observables": (ctypes.c_int, [_vp, _P(lb_obs)]),
     "lb_batch_get_fields": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
     "lb_batch_profile": (ctypes.c_int, [_vp, _i32, _vp, _sz, _dp]),
+    "lb_observables_static": (ctypes.c_int, [_P(lb_params), _vp, _d, _d, _d, _vp]),
 }
 
 
