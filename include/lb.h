@@ -58,6 +58,17 @@ extern "C" {
 #define LB_PERIODIC 0     /* periodic in x and y */
 #define LB_WALLS_Y 1      /* half-way bounce-back walls at y = -1/2 and y = ny - 1/2, periodic in x */
 
+/* Execution modes of the time loop (lb_set_config, lb_batch_set_config).
+ * LB_MODE_LAUNCH: each time step is a density-pass launch and a fused-kernel
+ *   launch over the tiles of all lattices, replayed 32 steps per CUDA graph.
+ * LB_MODE_PERSISTENT: one launch advances 64 time steps of all lattices; its
+ *   blocks take (step, phase, tile) work items from an atomic queue and wait,
+ *   with a bounded spin, only for the tiles of their own lattice that an item
+ *   depends on; replayed as a CUDA graph.  A wait that runs out (default 2 s)
+ *   ends the launch and the next synchronising call returns LB_ETIMEOUT. */
+#define LB_MODE_LAUNCH 0
+#define LB_MODE_PERSISTENT 1
+
 /* Densities the interaction stencils see beyond a wall (ghost rows
  * y = -1, -2 and y = ny, ny + 1). */
 #define LB_WALL_MIRROR 0  /* row -1 <- row 0, row -2 <- row 1, and symmetrically at the top */
@@ -146,8 +157,24 @@ int lb_set_fields_device(lb_handle *h, const double *rho, const double *u);
  * synchronising call (lb_observables, lb_get_fields, lb_synchronize). */
 int lb_step(lb_handle *h, int64_t n);
 
-/* Block until the handle's queued work has finished. */
+/* Block until the handle's queued work has finished.  Returns LB_ETIMEOUT
+ * (once) if a bounded device-side wait of a persistent launch expired. */
 int lb_synchronize(lb_handle *h);
+
+/* Execution configuration: mode (LB_MODE_LAUNCH or LB_MODE_PERSISTENT) and
+ * tile height (2, 4 or 8 nodes; tiles are 32 nodes wide, one thread per
+ * node).  Default: LB_MODE_LAUNCH, 4.  Results do not depend on it. */
+int lb_set_config(lb_handle *h, int32_t mode, int32_t tile_height);
+int lb_get_config(const lb_handle *h, int32_t *mode, int32_t *tile_height);
+
+/* Autotuner: times every mode and tile height on trial_steps time steps of
+ * the current state (the state is restored after each trial, so the lattice
+ * does not advance) and keeps the fastest.  With cache_path != NULL the
+ * choice is read from / appended to that text file, keyed by device name,
+ * precision and lattice shapes; a cached key skips the trials.  *best_ms
+ * (may be NULL) receives the time per step of the chosen configuration.
+ * Needs device memory for one copy of the state while it runs. */
+int lb_autotune(lb_handle *h, int32_t trial_steps, const char *cache_path, double *best_ms);
 
 /* Current time step count. */
 int64_t lb_time(const lb_handle *h);
@@ -215,6 +242,15 @@ int lb_batch_observables(lb_batch *b, lb_obs *o);
 int lb_batch_get_fields(lb_batch *b, int32_t i, double *rho, double *mom, double *ubar);
 /* As lb_profile, over all lattices of the batch (one launch covers them all). */
 int lb_batch_profile(lb_batch *b, int32_t nsteps, void *flush_buf, size_t flush_bytes, double ms[3]);
+/* As lb_set_config, lb_get_config and lb_autotune, for the whole batch. */
+int lb_batch_set_config(lb_batch *b, int32_t mode, int32_t tile_height);
+int lb_batch_get_config(const lb_batch *b, int32_t *mode, int32_t *tile_height);
+int lb_batch_autotune(lb_batch *b, int32_t trial_steps, const char *cache_path, double *best_ms);
+/* Limit of every bounded wait of the persistent kernel, in seconds (default
+ * 2).  drop_tile >= 0 is a test hook: that tile of the batch's tile list
+ * never reports completion, so the waits on it run out and the launch ends
+ * with LB_ETIMEOUT; -1 turns the hook off. */
+int lb_batch_set_wait_limit(lb_batch *b, double seconds, int32_t drop_tile);
 
 /* ---- observables without any allocation ------------------------------------ */
 

@@ -7,9 +7,13 @@
 // FP64 parameters (1/tau, (1 - 1/(2 tau)) w) round exactly as written.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <limits>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -40,6 +44,10 @@ int cuda_fail(cudaError_t e, const char *what)
     } while (0)
 
 constexpr int kGraphSteps = 32;   // steps per captured graph (even: parity returns)
+constexpr int kPersistSteps = 64; // time steps per persistent launch
+constexpr int kTileHeights[3] = {2, 4, 8};
+
+int ty_index(int ty) { return ty == 2 ? 0 : (ty == 4 ? 1 : (ty == 8 ? 2 : -1)); }
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -105,10 +113,26 @@ struct lb_engine {
     std::vector<lb_params> P;
     std::vector<lbk::Lat<double>> L64;
     std::vector<lbk::Lat<float>> L32;
-    std::vector<int4> tiles;
+    std::vector<int4> tiles;          // 32 x 4 tiles of the observation kernels
     void *d_lats = nullptr;
     int4 *d_tiles = nullptr;
+    // time-step tiles for each tile height (2, 4, 8) and per-lattice counts
+    std::vector<int4> stiles[3];
+    int4 *d_stiles[3] = {nullptr, nullptr, nullptr};
+    int *d_sntiles[3] = {nullptr, nullptr, nullptr};
+    // execution configuration (autotuned or set by the caller)
+    int mode = LB_MODE_LAUNCH;
+    int ty = 4;
+    // persistent launches: control block (queue head + per-lattice counters),
+    // sticky error word, blocks per SM per tile height, bounded-wait limit
+    void *d_ctl = nullptr;
+    int *d_err = nullptr;
+    int sm_count = 0;
+    int persist_bps[3] = {0, 0, 0};
+    long long wait_cycles = 0;
+    int drop_tile = -1;
     void *d_pool = nullptr;
+    size_t pool_bytes = 0;
     double *d_partials = nullptr;
     double *d_obs = nullptr;
     double *d_tmp = nullptr;
@@ -123,6 +147,12 @@ struct lb_engine {
         if (gexec) cudaGraphExecDestroy(gexec);
         cudaFree(d_lats);
         cudaFree(d_tiles);
+        for (int i = 0; i < 3; ++i) {
+            cudaFree(d_stiles[i]);
+            cudaFree(d_sntiles[i]);
+        }
+        cudaFree(d_ctl);
+        cudaFree(d_err);
         cudaFree(d_pool);
         cudaFree(d_partials);
         cudaFree(d_obs);
@@ -156,24 +186,75 @@ struct lb_engine {
     }
     int end() { return LB_OK; }
 
-    cudaError_t launch_density(int par, int off, int cnt)
+    // density pass over tiles of the observation list (height 4)
+    cudaError_t launch_density_obs(int par, int off, int cnt)
     {
         if (precision == LB_FP64)
-            return lbk::Launch<double>::density((const lbk::Lat<double> *)d_lats, d_tiles, off, cnt, par, stream);
-        return lbk::Launch<float>::density((const lbk::Lat<float> *)d_lats, d_tiles, off, cnt, par, stream);
+            return lbk::Launch<double>::density((const lbk::Lat<double> *)d_lats, d_tiles, off, cnt, par, 4, stream);
+        return lbk::Launch<float>::density((const lbk::Lat<float> *)d_lats, d_tiles, off, cnt, par, 4, stream);
     }
-    cudaError_t launch_collide(int par, int off, int cnt)
-    {
-        if (precision == LB_FP64)
-            return lbk::Launch<double>::collide((const lbk::Lat<double> *)d_lats, d_tiles, off, cnt, par, stream);
-        return lbk::Launch<float>::collide((const lbk::Lat<float> *)d_lats, d_tiles, off, cnt, par, stream);
-    }
+    // one time step as two launches over the time-step tiles of height ty
     cudaError_t launch_step(int par)
     {
-        const int nt = (int)tiles.size();
-        cudaError_t e = launch_density(par, 0, nt);
+        const int ti = ty_index(ty), nt = (int)stiles[ti].size();
+        cudaError_t e;
+        if (precision == LB_FP64) {
+            const lbk::Lat<double> *L = (const lbk::Lat<double> *)d_lats;
+            e = lbk::Launch<double>::density(L, d_stiles[ti], 0, nt, par, ty, stream);
+            if (e == cudaSuccess) e = lbk::Launch<double>::collide(L, d_stiles[ti], 0, nt, par, ty, stream);
+        } else {
+            const lbk::Lat<float> *L = (const lbk::Lat<float> *)d_lats;
+            e = lbk::Launch<float>::density(L, d_stiles[ti], 0, nt, par, ty, stream);
+            if (e == cudaSuccess) e = lbk::Launch<float>::collide(L, d_stiles[ti], 0, nt, par, ty, stream);
+        }
+        return e;
+    }
+    size_t ctl_bytes() const { return 8 + 2 * sizeof(unsigned) * (size_t)n; }
+    // nsteps time steps in one persistent launch (counters cleared first)
+    cudaError_t launch_persistent(int par, int nsteps)
+    {
+        const int ti = ty_index(ty), nt = (int)stiles[ti].size();
+        cudaError_t e = cudaMemsetAsync(d_ctl, 0, ctl_bytes(), stream);
         if (e != cudaSuccess) return e;
-        return launch_collide(par, 0, nt);
+        unsigned *dens = (unsigned *)((char *)d_ctl + 8), *coll = dens + n;
+        int blocks = persist_bps[ti] * sm_count;
+        if (blocks <= 0) blocks = sm_count > 0 ? sm_count : 1;
+        if (precision == LB_FP64)
+            return lbk::Launch<double>::persistent((const lbk::Lat<double> *)d_lats, d_stiles[ti], d_sntiles[ti], nt,
+                                                   nsteps, par, d_ctl, dens, coll, d_err, wait_cycles, drop_tile, ty,
+                                                   blocks, stream);
+        return lbk::Launch<float>::persistent((const lbk::Lat<float> *)d_lats, d_stiles[ti], d_sntiles[ti], nt,
+                                              nsteps, par, d_ctl, dens, coll, d_err, wait_cycles, drop_tile, ty,
+                                              blocks, stream);
+    }
+    // time steps in the current mode, as captured into one graph
+    cudaError_t launch_chunk(int par, int nsteps)
+    {
+        if (mode == LB_MODE_PERSISTENT) return launch_persistent(par, nsteps);
+        cudaError_t e = cudaSuccess;
+        for (int s = 0; s < nsteps && e == cudaSuccess; ++s) e = launch_step((par + s) & 1);
+        return e;
+    }
+    int chunk_steps() const { return mode == LB_MODE_PERSISTENT ? kPersistSteps : kGraphSteps; }
+    void drop_graph()
+    {
+        if (gexec) {
+            cudaGraphExecDestroy(gexec);
+            gexec = nullptr;
+        }
+    }
+    // a bounded device-side wait that ran out is reported once, then cleared
+    int check_timeout()
+    {
+        int h = 0;
+        LB_CUDA(cudaMemcpyAsync(&h, d_err, sizeof h, cudaMemcpyDeviceToHost, stream));
+        LB_CUDA(cudaStreamSynchronize(stream));
+        if (h) {
+            LB_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), stream));
+            LB_CUDA(cudaStreamSynchronize(stream));
+            return fail(LB_ETIMEOUT, "a bounded wait of the persistent kernel expired; the state is invalid");
+        }
+        return LB_OK;
     }
     cudaError_t launch_observe(int par, int off, int cnt, double *partials, double *rho, double *mom, double *ubar)
     {
@@ -211,8 +292,7 @@ struct lb_engine {
     {
         cudaGraph_t g = nullptr;
         LB_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t le = cudaSuccess;
-        for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s) le = launch_step(s & 1);
+        cudaError_t le = launch_chunk(0, chunk_steps());
         cudaError_t ce = cudaStreamEndCapture(stream, &g);
         if (le != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -233,20 +313,32 @@ struct lb_engine {
         if (nsteps < 0) return fail(LB_EINVAL, "negative step count");
         int rc = begin();
         if (rc) return rc;
+        const int chunk = chunk_steps();
         while (nsteps > 0) {
-            if (parity == 0 && nsteps >= kGraphSteps) {
+            if (parity == 0 && nsteps >= chunk) {
                 if (!gexec && (rc = build_graph())) return rc;
                 LB_CUDA(cudaGraphLaunch(gexec, stream));
-                nsteps -= kGraphSteps;
-                t += kGraphSteps;
+                nsteps -= chunk;
+                t += chunk;
             } else {
-                LB_CUDA(launch_step(parity));
-                parity ^= 1;
-                nsteps -= 1;
-                t += 1;
+                const int k = mode == LB_MODE_PERSISTENT ? (int)std::min<int64_t>(nsteps, parity ? 1 : chunk) : 1;
+                LB_CUDA(launch_chunk(parity, k));
+                parity ^= (k & 1);
+                nsteps -= k;
+                t += k;
             }
         }
         return end();
+    }
+
+    int set_config(int m, int tyv)
+    {
+        if (m != LB_MODE_LAUNCH && m != LB_MODE_PERSISTENT) return fail(LB_EINVAL, "mode must be LB_MODE_LAUNCH or LB_MODE_PERSISTENT");
+        if (ty_index(tyv) < 0) return fail(LB_EINVAL, "tile height must be 2, 4 or 8");
+        if (m != mode || tyv != ty) drop_graph();
+        mode = m;
+        ty = tyv;
+        return LB_OK;
     }
 
     int profile(int32_t nsteps, void *flush, size_t flush_bytes, double ms[3])
@@ -265,14 +357,22 @@ struct lb_engine {
                 cleanup();
                 return fail(LB_ECUDA, "cudaEventCreate failed");
             }
-        const int nt = (int)tiles.size();
+        const int ti = ty_index(ty), nt = (int)stiles[ti].size();
         cudaError_t ce = cudaSuccess;
         for (int s = 0; s < nsteps && ce == cudaSuccess; ++s) {
             if (flush_bytes) ce = cudaMemsetAsync(flush, s & 0xff, flush_bytes, stream);
             if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s], stream);
-            if (ce == cudaSuccess) ce = launch_density(parity, 0, nt);
-            if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s + 1], stream);
-            if (ce == cudaSuccess) ce = launch_collide(parity, 0, nt);
+            if (precision == LB_FP64) {
+                const lbk::Lat<double> *L = (const lbk::Lat<double> *)d_lats;
+                if (ce == cudaSuccess) ce = lbk::Launch<double>::density(L, d_stiles[ti], 0, nt, parity, ty, stream);
+                if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s + 1], stream);
+                if (ce == cudaSuccess) ce = lbk::Launch<double>::collide(L, d_stiles[ti], 0, nt, parity, ty, stream);
+            } else {
+                const lbk::Lat<float> *L = (const lbk::Lat<float> *)d_lats;
+                if (ce == cudaSuccess) ce = lbk::Launch<float>::density(L, d_stiles[ti], 0, nt, parity, ty, stream);
+                if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s + 1], stream);
+                if (ce == cudaSuccess) ce = lbk::Launch<float>::collide(L, d_stiles[ti], 0, nt, parity, ty, stream);
+            }
             if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s + 2], stream);
             if (ce == cudaSuccess) {
                 parity ^= 1;
@@ -296,12 +396,125 @@ struct lb_engine {
         return end();
     }
 
+    // key of the autotuning cache: device, precision and lattice shapes
+    std::string tune_key() const
+    {
+        cudaDeviceProp prop;
+        std::string dev = "unknown";
+        if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) dev = prop.name;
+        for (char &c : dev)
+            if (c == ' ' || c == '\t') c = '_';
+        unsigned long long h = 1469598103934665603ull;   // FNV-1a over the shapes
+        auto mix = [&](long long v) {
+            for (int b = 0; b < 8; ++b) {
+                h ^= (unsigned long long)((v >> (8 * b)) & 0xff);
+                h *= 1099511628211ull;
+            }
+        };
+        for (const lb_params &p : P) {
+            mix(p.nx);
+            mix(p.ny);
+            mix(p.walls);
+        }
+        std::ostringstream os;
+        os << dev << "|" << (precision == LB_FP64 ? "fp64" : "fp32") << "|n" << n << "|" << std::hex << h;
+        return os.str();
+    }
+
+    // Time every (mode, tile height) on trial_steps steps of the current state
+    // (restored after each trial) and keep the fastest; results are cached in
+    // cache_path (one "key mode ty ms" line per configuration) when given.
+    int autotune(int trial_steps, const char *cache_path, double *best_ms)
+    {
+        if (trial_steps < 1) return fail(LB_EINVAL, "trial_steps must be >= 1");
+        const std::string key = tune_key();
+        std::vector<std::string> lines;
+        if (cache_path) {
+            std::ifstream in(cache_path);
+            std::string ln;
+            while (std::getline(in, ln)) {
+                std::istringstream is(ln);
+                std::string k;
+                int m = -1, tyv = -1;
+                double ms = 0.0;
+                if (!(is >> k >> m >> tyv >> ms)) continue;
+                if (k == key && set_config(m, tyv) == LB_OK) {
+                    if (best_ms) *best_ms = ms;
+                    return LB_OK;
+                }
+                lines.push_back(ln);
+            }
+        }
+        int rc = begin();
+        if (rc) return rc;
+        void *snap = nullptr;
+        if (cudaMalloc(&snap, pool_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LB_ENOMEM, "autotune: no room for a snapshot of the state");
+        }
+        const int64_t t0 = t;
+        const int par0 = parity;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        double best = std::numeric_limits<double>::infinity();
+        int bm = mode, bty = ty;
+        cudaError_t ce = cudaMemcpyAsync(snap, d_pool, pool_bytes, cudaMemcpyDeviceToDevice, stream);
+        for (int m = LB_MODE_LAUNCH; m <= LB_MODE_PERSISTENT && ce == cudaSuccess && rc == LB_OK; ++m)
+            for (int tyv : kTileHeights) {
+                if ((rc = set_config(m, tyv))) break;
+                if ((rc = step(chunk_steps()))) break;            // warm-up, builds the graph
+                ce = cudaEventRecord(e0, stream);
+                if (ce == cudaSuccess && (rc = step(trial_steps))) break;
+                if (ce == cudaSuccess) ce = cudaEventRecord(e1, stream);
+                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+                if (ce != cudaSuccess) break;
+                if ((rc = check_timeout())) break;
+                const double per = (double)ms / trial_steps;
+                if (per < best) {
+                    best = per;
+                    bm = m;
+                    bty = tyv;
+                }
+                ce = cudaMemcpyAsync(d_pool, snap, pool_bytes, cudaMemcpyDeviceToDevice, stream);
+                t = t0;
+                parity = par0;
+            }
+        cudaStreamSynchronize(stream);
+        cudaMemcpy(d_pool, snap, pool_bytes, cudaMemcpyDeviceToDevice);
+        t = t0;
+        parity = par0;
+        cudaFree(snap);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) return rc;
+        if (ce != cudaSuccess) return cuda_fail(ce, "autotune trial");
+        set_config(bm, bty);
+        if (best_ms) *best_ms = best;
+        if (cache_path) {
+            std::ostringstream os;
+            os << key << " " << bm << " " << bty << " " << best;
+            lines.push_back(os.str());
+            const std::string tmp = std::string(cache_path) + ".tmp";
+            {
+                std::ofstream out(tmp, std::ios::trunc);
+                for (const auto &ln : lines) out << ln << "\n";
+                if (!out) return fail(LB_EINVAL, "autotune: cannot write the cache file");
+            }
+            if (std::rename(tmp.c_str(), cache_path) != 0) return fail(LB_EINVAL, "autotune: cannot replace the cache file");
+        }
+        return end();
+    }
+
     int observables(lb_obs *o)
     {
         int rc = begin();
         if (rc) return rc;
         const int nt = (int)tiles.size();
-        LB_CUDA(launch_density(parity, 0, nt));
+        if ((rc = check_timeout())) return rc;
+        LB_CUDA(launch_density_obs(parity, 0, nt));
         LB_CUDA(launch_observe(parity, 0, nt, d_partials, nullptr, nullptr, nullptr));
         LB_CUDA(launch_finalize());
         std::vector<double> h((size_t)n * lbk::kObsStride);
@@ -339,7 +552,7 @@ struct lb_engine {
         int rc = begin();
         if (rc) return rc;
         if ((rc = ensure_tmp(8 * cells))) return rc;
-        LB_CUDA(launch_density(parity, tile_begin(l), tile_end(l) - tile_begin(l)));
+        LB_CUDA(launch_density_obs(parity, tile_begin(l), tile_end(l) - tile_begin(l)));
         LB_CUDA(launch_observe(parity, tile_begin(l), tile_end(l) - tile_begin(l), nullptr, d_tmp, d_tmp + 2 * cells,
                                d_tmp + 6 * cells));
         if (rho) LB_CUDA(cudaMemcpyAsync(rho, d_tmp, 2 * cells * sizeof(double), cudaMemcpyDeviceToHost, stream));
@@ -480,6 +693,7 @@ int engine_create(const lb_params *p, int n, lb_engine **out)
         off_r1[l] = total;
         total = align_up(total + 2 * plane * rs, kAlign);
     }
+    e->pool_bytes = total;
     if (cudaMalloc(&e->d_pool, total) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(LB_ENOMEM, "cudaMalloc of the lattice state failed"));
@@ -523,6 +737,42 @@ int engine_create(const lb_params *p, int n, lb_engine **out)
         cudaMalloc((void **)&e->d_obs, (size_t)n * lbk::kObsStride * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(LB_ENOMEM, "cudaMalloc of the descriptors failed"));
+    }
+    // time-step tiles for every supported tile height, and the persistent
+    // launch's control block and error word
+    for (int ti = 0; ti < 3; ++ti) {
+        const int tyv = kTileHeights[ti];
+        std::vector<int> counts(n, 0);
+        for (int l = 0; l < n; ++l) {
+            const size_t before = e->stiles[ti].size();
+            for (int y0 = 0; y0 < p[l].ny; y0 += tyv)
+                for (int x0 = 0; x0 < p[l].nx; x0 += lbk::TX) e->stiles[ti].push_back(make_int4(l, x0, y0, 0));
+            counts[l] = (int)(e->stiles[ti].size() - before);
+        }
+        if (cudaMalloc((void **)&e->d_stiles[ti], e->stiles[ti].size() * sizeof(int4)) != cudaSuccess ||
+            cudaMalloc((void **)&e->d_sntiles[ti], n * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(LB_ENOMEM, "cudaMalloc of the tile lists failed"));
+        }
+        if ((ce = cudaMemcpyAsync(e->d_stiles[ti], e->stiles[ti].data(), e->stiles[ti].size() * sizeof(int4),
+                                  cudaMemcpyHostToDevice, e->stream)) != cudaSuccess ||
+            (ce = cudaMemcpyAsync(e->d_sntiles[ti], counts.data(), n * sizeof(int), cudaMemcpyHostToDevice,
+                                  e->stream)) != cudaSuccess ||
+            (ce = cudaStreamSynchronize(e->stream)) != cudaSuccess)
+            return bail(cuda_fail(ce, "tile list upload"));
+        e->persist_bps[ti] = e->precision == LB_FP64 ? lbk::Launch<double>::persistent_blocks_per_sm(tyv)
+                                                     : lbk::Launch<float>::persistent_blocks_per_sm(tyv);
+    }
+    if (cudaMalloc(&e->d_ctl, e->ctl_bytes()) != cudaSuccess || cudaMalloc((void **)&e->d_err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(LB_ENOMEM, "cudaMalloc of the persistent control block failed"));
+    }
+    if ((ce = cudaMemsetAsync(e->d_err, 0, sizeof(int), e->stream)) != cudaSuccess) return bail(cuda_fail(ce, "cudaMemsetAsync"));
+    {
+        int khz = 0;
+        cudaDeviceGetAttribute(&e->sm_count, cudaDevAttrMultiProcessorCount, e->device);
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, e->device);
+        e->wait_cycles = (long long)(2.0 * (khz > 0 ? khz : 2000000) * 1000.0);   // 2 s
     }
     if ((ce = cudaMemcpyAsync(e->d_lats, lat_src, lat_bytes, cudaMemcpyHostToDevice, e->stream)) != cudaSuccess ||
         (ce = cudaMemcpyAsync(e->d_tiles, e->tiles.data(), e->tiles.size() * sizeof(int4), cudaMemcpyHostToDevice,
@@ -610,7 +860,27 @@ int lb_synchronize(lb_handle *h)
     CHECK_H(h);
     cudaError_t ce = cudaStreamSynchronize(h->e->stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
+    return h->e->check_timeout();
+}
+
+int lb_set_config(lb_handle *h, int32_t mode, int32_t tile_height)
+{
+    CHECK_H(h);
+    return h->e->set_config(mode, tile_height);
+}
+
+int lb_get_config(const lb_handle *h, int32_t *mode, int32_t *tile_height)
+{
+    if (!h || !h->e || !mode || !tile_height) return fail(LB_EINVAL, "NULL argument");
+    *mode = h->e->mode;
+    *tile_height = h->e->ty;
     return LB_OK;
+}
+
+int lb_autotune(lb_handle *h, int32_t trial_steps, const char *cache_path, double *best_ms)
+{
+    CHECK_H(h);
+    return h->e->autotune(trial_steps, cache_path, best_ms);
 }
 
 int64_t lb_time(const lb_handle *h) { return (h && h->e) ? h->e->t : -1; }
@@ -757,6 +1027,38 @@ int lb_batch_synchronize(lb_batch *b)
     CHECK_B(b, 0);
     cudaError_t ce = cudaStreamSynchronize(b->e->stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
+    return b->e->check_timeout();
+}
+
+int lb_batch_set_config(lb_batch *b, int32_t mode, int32_t tile_height)
+{
+    CHECK_B(b, 0);
+    return b->e->set_config(mode, tile_height);
+}
+
+int lb_batch_get_config(const lb_batch *b, int32_t *mode, int32_t *tile_height)
+{
+    if (!b || !b->e || !mode || !tile_height) return fail(LB_EINVAL, "NULL argument");
+    *mode = b->e->mode;
+    *tile_height = b->e->ty;
+    return LB_OK;
+}
+
+int lb_batch_autotune(lb_batch *b, int32_t trial_steps, const char *cache_path, double *best_ms)
+{
+    CHECK_B(b, 0);
+    return b->e->autotune(trial_steps, cache_path, best_ms);
+}
+
+int lb_batch_set_wait_limit(lb_batch *b, double seconds, int32_t drop_tile)
+{
+    CHECK_B(b, 0);
+    if (!(seconds > 0.0) || !std::isfinite(seconds)) return fail(LB_EINVAL, "wait limit must be finite and > 0");
+    int khz = 0;
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, b->e->device);
+    b->e->wait_cycles = (long long)(seconds * (khz > 0 ? khz : 2000000) * 1000.0);
+    b->e->drop_tile = drop_tile < 0 ? -1 : drop_tile;
+    b->e->drop_graph();
     return LB_OK;
 }
 

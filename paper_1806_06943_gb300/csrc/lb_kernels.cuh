@@ -33,11 +33,14 @@
 namespace lbk {
 
 constexpr int TX = 32;           // tile width = threads in x
-constexpr int TY = 4;            // tile height = threads in y
+constexpr int TY = 4;            // tile height of the observation kernels = threads in y
 constexpr int HALO = 2;          // reach of the D2Q25 stencil
 constexpr int SW = TX + 2 * HALO;
 constexpr int SH = TY + 2 * HALO;
 constexpr int kThreads = TX * TY;
+// Tile heights the time-step kernels are built for (chosen per batch by the
+// autotuner); one thread per node, 32 nodes wide.
+constexpr int kTileHeights[3] = {2, 4, 8};
 
 template <typename real>
 constexpr bool kOffset = sizeof(real) == 4;
@@ -45,8 +48,8 @@ constexpr bool kOffset = sizeof(real) == 4;
 // Resident blocks per SM the fused kernel is compiled for: the FP32 kernel is
 // bound by HBM and needs the warps to keep enough loads in flight; the FP64
 // kernel is bound by the FP64 pipe and keeps its registers.
-template <typename real>
-constexpr int kCollideMinBlocks = kOffset<real> ? 8 : 4;
+template <typename real, int TYv>
+constexpr int kCollideMinBlocks = (kOffset<real> ? 32 : 16) / TYv;
 
 // ---- lattice tables (Sec. II A; Fig. 1; Sec. II B after Eq. 8) ------------
 // D2Q9 order: rest, (1,0), (0,1), (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1).
@@ -82,16 +85,17 @@ __device__ __forceinline__ int wrap_index(int a, int n)
 // density copy `rho`.  Periodic copies in x (and in y without walls); beyond a
 // wall the ghost rows are either mirrored from the fluid or set to the fixed
 // wall densities.
-template <typename real>
+template <typename real, int SHv>
 __device__ __forceinline__ void stage_tile(const Lat<real> &L, const real *__restrict__ rho, int x0, int y0,
-                                           real (*srho)[SH][SW], real (*spsi)[SH][SW], int tid, int nthreads)
+                                           real (*srho)[SHv][SW], real (*spsi)[SHv][SW], int tid, int nthreads)
 {
+    constexpr int TYv = SHv - 2 * HALO;
     const int nx = L.nx, ny = L.ny;
     // tiles whose halo lies inside the lattice need no wrapping or ghosts
-    const bool inner = x0 >= HALO && x0 + TX + HALO <= nx && y0 >= HALO && y0 + TY + HALO <= ny;
+    const bool inner = x0 >= HALO && x0 + TX + HALO <= nx && y0 >= HALO && y0 + TYv + HALO <= ny;
     if (inner) {
         const real *__restrict__ base = rho + (size_t)(y0 - HALO) * L.pitch + (x0 - HALO);
-        for (int idx = tid; idx < SW * SH; idx += nthreads) {
+        for (int idx = tid; idx < SW * SHv; idx += nthreads) {
             const int sx = idx % SW, sy = idx / SW;
             const size_t c = (size_t)sy * L.pitch + sx;
             const real rA = base[c], rB = base[L.plane + c];
@@ -102,7 +106,7 @@ __device__ __forceinline__ void stage_tile(const Lat<real> &L, const real *__res
         }
         return;
     }
-    for (int idx = tid; idx < SW * SH; idx += nthreads) {
+    for (int idx = tid; idx < SW * SHv; idx += nthreads) {
         const int sx = idx % SW, sy = idx / SW;
         const int gx = wrap_index(x0 + sx - HALO, nx);
         int gy = y0 + sy - HALO;
@@ -197,8 +201,8 @@ __device__ __forceinline__ void q25_sum(const real (*s)[SW], int cx, int cy, rea
 }
 
 // Total force on species k at the staged node (cx, cy): Eq. (8) + Eq. (9) + rho_k g.
-template <typename real>
-__device__ __forceinline__ void force_at(const Lat<real> &L, const real (*srho)[SH][SW], const real (*spsi)[SH][SW],
+template <typename real, int SHv>
+__device__ __forceinline__ void force_at(const Lat<real> &L, const real (*srho)[SHv][SW], const real (*spsi)[SHv][SW],
                                          int k, int cx, int cy, real &Fx, real &Fy)
 {
     real s1x, s1y, s2x, s2y, s3x, s3y;
@@ -253,8 +257,8 @@ __device__ __forceinline__ real collide_dir(real f, real rho, real ux, real uy, 
 // Store the post-collision value of direction I of species k at x + e_i
 // (half-way bounce-back: back to x, reversed).  FP32: re-reference the offset
 // from rho(x) to rho(x + e_i), the reference the next step reads there.
-template <typename real, int I, bool kInner>
-__device__ __forceinline__ void push_dir(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SH][SW], int k,
+template <typename real, int I, bool kInner, int SHv>
+__device__ __forceinline__ void push_dir(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW], int k,
                                          int x, int y, int cx, int cy, real v)
 {
     constexpr int EX = ex9(I), EY = ey9(I);
@@ -297,8 +301,8 @@ struct SpeciesTerms {
     real aw3[2][3];    // 3 (1 - omega_k/2) w(|e|^2)
 };
 
-template <typename real, int I, bool kInner>
-__device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SH][SW],
+template <typename real, int I, bool kInner, int SHv>
+__device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW],
                                                  const real (&fk)[2][9], const real (&rho)[2], real ux, real uy, real uu,
                                                  const real (&F)[2][2], const SpeciesTerms<real> &st, int x, int y,
                                                  int cx, int cy)
@@ -309,7 +313,7 @@ __device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__res
         for (int k = 0; k < 2; ++k) {
             const real v = collide_dir<real, I>(fk[k][I], rho[k], ux, uy, uu, F[k][0], F[k][1], L.omega[k],
                                                 L.aw[k][cls9(I)]);
-            push_dir<real, I, kInner>(L, fn, srho, k, x, y, cx, cy, v);
+            push_dir<real, I, kInner, SHv>(L, fn, srho, k, x, y, cx, cy, v);
         }
     } else {
         // Eq. (2) less w rho (the node's own density is the offset), and Eq. (5)
@@ -326,7 +330,7 @@ __device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__res
             const real geq = st.wr[k][C] * q;
             const real f = fk[k][I];
             const real v = (f + L.omega[k] * (geq - f)) + Cg;
-            push_dir<real, I, kInner>(L, fn, srho, k, x, y, cx, cy, v);
+            push_dir<real, I, kInner, SHv>(L, fn, srho, k, x, y, cx, cy, v);
         }
     }
 }
@@ -358,13 +362,20 @@ __device__ __forceinline__ real zeroth_moment(const real (&f)[9])
 
 // ---- kernels ----------------------------------------------------------------
 
-// rho_k = sum_i f_k,i into density copy parity^1 (FP32: R + sum_i h_i, R the
-// density of the previous step in copy parity).
-template <typename real>
-__global__ void __launch_bounds__(kThreads) k_density(const Lat<real> *__restrict__ lats, const int4 *__restrict__ tiles,
-                                                      int tile_offset, int parity)
+// Global loads of data that other blocks of the same launch may have written
+// (the persistent kernel): through L2 only, never a stale L1 line.
+template <bool kCG, typename real>
+__device__ __forceinline__ real ldg_state(const real *p)
 {
-    const int4 t = tiles[tile_offset + blockIdx.x];
+    if constexpr (kCG) return __ldcg(p);
+    else return *p;
+}
+
+// rho_k = sum_i f_k,i of one tile into density copy parity^1 (FP32: R +
+// sum_i h_i, R the density of the previous step in copy parity).
+template <typename real, int TYv, bool kCG>
+__device__ __forceinline__ void density_tile(const Lat<real> *__restrict__ lats, int4 t, int parity)
+{
     const Lat<real> &L = lats[t.x];
     const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
     if (x >= L.nx || y >= L.ny) return;
@@ -374,61 +385,118 @@ __global__ void __launch_bounds__(kThreads) k_density(const Lat<real> *__restric
     for (int k = 0; k < 2; ++k) {
         real v[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) v[i] = f[(size_t)(k * 9 + i) * L.plane + c];
+        for (int i = 0; i < 9; ++i) v[i] = ldg_state<kCG>(&f[(size_t)(k * 9 + i) * L.plane + c]);
         real r = zeroth_moment<real>(v);
-        if constexpr (kOffset<real>) r = L.rho[parity][(size_t)k * L.plane + c] + r;
+        if constexpr (kOffset<real>) r = ldg_state<kCG>(&L.rho[parity][(size_t)k * L.plane + c]) + r;
         L.rho[parity ^ 1][(size_t)k * L.plane + c] = r;
     }
 }
 
-template <typename real, bool kInner>
-__device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SH][SW],
-                                             const real (*spsi)[SH][SW], real (&fk)[2][9], int x, int y, int cx, int cy);
-
-// Fused force + collision + push-streaming + bounce-back for one tile.
-template <typename real>
-__global__ void __launch_bounds__(kThreads, kCollideMinBlocks<real>) k_collide(const Lat<real> *__restrict__ lats, const int4 *__restrict__ tiles,
-                                                      int tile_offset, int parity)
+template <typename real, int TYv>
+__global__ void __launch_bounds__(TX *TYv) k_density(const Lat<real> *__restrict__ lats, const int4 *__restrict__ tiles,
+                                                     int tile_offset, int parity)
 {
-    __shared__ real srho[2][SH][SW];
-    __shared__ real spsi[2][SH][SW];
-    __shared__ Lat<real> sL;   // descriptor copy: stores to fn cannot alias it
-    const int4 t = tiles[tile_offset + blockIdx.x];
+    density_tile<real, TYv, false>(lats, tiles[tile_offset + blockIdx.x], parity);
+}
+
+// Shared memory of the fused kernel for a tile of height TYv.
+template <typename real, int TYv>
+struct CollideSmem {
+    real srho[2][TYv + 2 * HALO][SW];
+    real spsi[2][TYv + 2 * HALO][SW];
+    Lat<real> L;   // descriptor copy: stores to the populations cannot alias it
+};
+
+template <typename real, bool kInner, int SHv>
+__device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW],
+                                             const real (*spsi)[SHv][SW], real (&fk)[2][9], int x, int y, int cx, int cy);
+
+// Fused force + collision + push-streaming + bounce-back for one tile.  Every
+// thread of the block calls it and returns from it; it ends after the tile's
+// pushes are issued (the caller synchronises before reusing sm).
+template <typename real, int TYv, bool kCG>
+__device__ __forceinline__ void collide_tile(const Lat<real> *__restrict__ lats, int4 t, int parity,
+                                             CollideSmem<real, TYv> &sm)
+{
     const Lat<real> &G = lats[t.x];
     const int tid = threadIdx.y * TX + threadIdx.x;
     static_assert(sizeof(Lat<real>) % 4 == 0, "descriptor copied as 32-bit words");
     if (tid < (int)(sizeof(Lat<real>) / 4))
-        reinterpret_cast<uint32_t *>(&sL)[tid] = reinterpret_cast<const uint32_t *>(&G)[tid];
+        reinterpret_cast<uint32_t *>(&sm.L)[tid] = reinterpret_cast<const uint32_t *>(&G)[tid];
     const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
     const bool valid = x < G.nx && y < G.ny;
-    const Lat<real> &L = G;
     // issue the population loads first so their latency overlaps the staging
-    const real *__restrict__ fc = L.f[parity];
-    real *__restrict__ fn = L.f[parity ^ 1];
-    const size_t c = valid ? (size_t)y * L.pitch + x : 0;
+    const real *__restrict__ fc = G.f[parity];
+    real *__restrict__ fn = G.f[parity ^ 1];
+    const size_t c = valid ? (size_t)y * G.pitch + x : 0;
     real fk[2][9];
 #pragma unroll
     for (int k = 0; k < 2; ++k)
 #pragma unroll
-        for (int i = 0; i < 9; ++i) fk[k][i] = valid ? fc[(size_t)(k * 9 + i) * L.plane + c] : (real)0;
-    stage_tile<real>(L, L.rho[parity ^ 1], t.y, t.z, srho, spsi, tid, kThreads);
+        for (int i = 0; i < 9; ++i) fk[k][i] = valid ? ldg_state<kCG>(&fc[(size_t)(k * 9 + i) * G.plane + c]) : (real)0;
+    if constexpr (kCG) {
+        // staging reads the density copy through L2 as well
+        constexpr int SHv = TYv + 2 * HALO;
+        const int nx = G.nx, ny = G.ny;
+        const real *__restrict__ rho = G.rho[parity ^ 1];
+        for (int idx = tid; idx < SW * SHv; idx += TX * TYv) {
+            const int sx = idx % SW, sy = idx / SW;
+            const int gx = wrap_index(t.y + sx - HALO, nx);
+            int gy = t.z + sy - HALO;
+            real rA, rB;
+            bool fixed = false;
+            if (gy < 0 || gy >= ny) {
+                if (G.walls) {
+                    if (G.wall_mode == 1) {
+                        rA = G.wall_rho[0];
+                        rB = G.wall_rho[1];
+                        fixed = true;
+                    } else {
+                        gy = gy < 0 ? -1 - gy : 2 * ny - 1 - gy;
+                        gy = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
+                    }
+                } else {
+                    gy = wrap_index(gy, ny);
+                }
+            }
+            if (!fixed) {
+                const size_t cc = (size_t)gy * G.pitch + gx;
+                rA = __ldcg(&rho[cc]);
+                rB = __ldcg(&rho[G.plane + cc]);
+            }
+            sm.srho[0][sy][sx] = rA;
+            sm.srho[1][sy][sx] = rB;
+            sm.spsi[0][sy][sx] = psi_of<real>(rA);
+            sm.spsi[1][sy][sx] = psi_of<real>(rB);
+        }
+    } else {
+        stage_tile<real, TYv + 2 * HALO>(G, G.rho[parity ^ 1], t.y, t.z, sm.srho, sm.spsi, tid, TX * TYv);
+    }
     __syncthreads();
     if (!valid) return;
     const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
     // tiles whose pushes stay inside the lattice (no wrap, no wall) take constant offsets
-    const bool inner = t.y >= 1 && t.y + TX + 1 <= sL.nx && t.z >= 1 && t.z + TY + 1 <= sL.ny;
-    if (inner) collide_site<real, true>(sL, fn, srho, spsi, fk, x, y, cx, cy);
-    else collide_site<real, false>(sL, fn, srho, spsi, fk, x, y, cx, cy);
+    const bool inner = t.y >= 1 && t.y + TX + 1 <= sm.L.nx && t.z >= 1 && t.z + TYv + 1 <= sm.L.ny;
+    if (inner) collide_site<real, true, TYv + 2 * HALO>(sm.L, fn, sm.srho, sm.spsi, fk, x, y, cx, cy);
+    else collide_site<real, false, TYv + 2 * HALO>(sm.L, fn, sm.srho, sm.spsi, fk, x, y, cx, cy);
 }
 
-template <typename real, bool kInner>
-__device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SH][SW],
-                                             const real (*spsi)[SH][SW], real (&fk)[2][9], int x, int y, int cx, int cy)
+template <typename real, int TYv>
+__global__ void __launch_bounds__(TX *TYv, kCollideMinBlocks<real, TYv>)
+    k_collide(const Lat<real> *__restrict__ lats, const int4 *__restrict__ tiles, int tile_offset, int parity)
+{
+    __shared__ CollideSmem<real, TYv> sm;
+    collide_tile<real, TYv, false>(lats, tiles[tile_offset + blockIdx.x], parity, sm);
+}
+
+template <typename real, bool kInner, int SHv>
+__device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW],
+                                             const real (*spsi)[SHv][SW], real (&fk)[2][9], int x, int y, int cx, int cy)
 {
     real F[2][2], rho[2], m[2][2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        force_at<real>(L, srho, spsi, k, cx, cy, F[k][0], F[k][1]);
+        force_at<real, SHv>(L, srho, spsi, k, cx, cy, F[k][0], F[k][1]);
         rho[k] = srho[k][cy][cx];
         real jx, jy;
         first_moment<real>(fk[k], jx, jy);     // FP32: the reference density adds no momentum
@@ -460,15 +528,92 @@ __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restric
         }
     }
 
-    collide_push_dir<real, 0, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 1, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 2, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 3, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 4, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 5, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 6, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 7, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 8, kInner>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 0, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 1, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 2, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 3, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 4, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 5, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 6, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 7, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 8, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+}
+
+// ---- persistent launch over many time steps -----------------------------------
+
+// Bounded wait until *ctr >= need.  Gives up when another block has flagged an
+// error or after `limit` SM clock cycles, then flags LB_ETIMEOUT in *err.
+__device__ __forceinline__ bool wait_geq(const unsigned *ctr, unsigned need, int *err, long long limit)
+{
+    if (need == 0) return true;
+    const long long start = clock64();
+    for (;;) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= need) return true;
+        if (*(volatile int *)err) return false;
+        if (clock64() - start > limit) {
+            atomicExch(err, 1);
+            return false;
+        }
+        __nanosleep(128);
+    }
+}
+
+// Control block of a persistent launch (device memory, cleared before each
+// launch): the work-queue head, then per-lattice counts of finished density
+// and fused tiles.  The error word lives separately and survives launches.
+struct PersistCtl {
+    unsigned long long head;
+};
+
+// Advance nsteps time steps of every lattice in one launch.  Work items are
+// (step, phase, tile) in this order, handed out by an atomic queue; an item
+// waits only for the items of its own lattice it depends on (the density
+// pass of step t waits for all fused tiles of step t-1, the fused tiles of
+// step t for all density tiles of step t).  Every item it waits for has a
+// smaller index and was claimed by a running block, so the wait always ends
+// unless a block fails to signal; then the bounded wait flags the error and
+// every block leaves.  drop_tile >= 0 makes that tile never signal (a test of
+// the timeout path).
+template <typename real, int TYv>
+__global__ void __launch_bounds__(TX *TYv, kCollideMinBlocks<real, TYv>)
+    k_persistent(const Lat<real> *__restrict__ lats, const int4 *__restrict__ tiles, const int *__restrict__ lat_ntiles,
+                 int n_tiles, int nsteps, int parity0, PersistCtl *ctl, unsigned *dens_done, unsigned *coll_done,
+                 int *err, long long wait_cycles, int drop_tile)
+{
+    __shared__ CollideSmem<real, TYv> sm;
+    __shared__ long long s_item;
+    __shared__ int s_ok;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const long long total = (long long)nsteps * 2 * n_tiles;
+    for (;;) {
+        if (tid == 0) s_item = (long long)atomicAdd(&ctl->head, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        const int t = (int)(item / (2 * n_tiles));
+        const int r = (int)(item % (2 * n_tiles));
+        const int phase = r / n_tiles, tile = r % n_tiles;
+        const int4 tl = tiles[tile];
+        const int nt_l = lat_ntiles[tl.x];
+        const int parity = (parity0 + t) & 1;
+        if (tid == 0) {
+            const bool ok = phase == 0 ? wait_geq(&coll_done[tl.x], (unsigned)(t * nt_l), err, wait_cycles)
+                                       : wait_geq(&dens_done[tl.x], (unsigned)((t + 1) * nt_l), err, wait_cycles);
+            __threadfence();
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        if (phase == 0) density_tile<real, TYv, true>(lats, tl, parity);
+        else collide_tile<real, TYv, true>(lats, tl, parity, sm);
+        __syncthreads();
+        if (tid == 0 && tile != drop_tile) {
+            __threadfence();
+            atomicAdd(phase == 0 ? &dens_done[tl.x] : &coll_done[tl.x], 1u);
+        }
+    }
 }
 
 // ---- observables ------------------------------------------------------------
@@ -503,7 +648,7 @@ __global__ void __launch_bounds__(kThreads) k_observe(const Lat<real> *__restric
     const int4 t = tiles[tile_offset + blockIdx.x];
     const Lat<real> &L = lats[t.x];
     const int tid = threadIdx.y * TX + threadIdx.x;
-    stage_tile<real>(L, L.rho[parity ^ 1], t.y, t.z, srho, spsi, tid, kThreads);
+    stage_tile<real, SH>(L, L.rho[parity ^ 1], t.y, t.z, srho, spsi, tid, kThreads);
     __syncthreads();
     const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
     double acc[kNumAcc];
@@ -520,7 +665,7 @@ __global__ void __launch_bounds__(kThreads) k_observe(const Lat<real> *__restric
 #pragma unroll
             for (int i = 0; i < 9; ++i) fk[i] = fc[(size_t)(k * 9 + i) * L.plane + c];
             real Fx, Fy, jx, jy;
-            force_at<real>(L, srho, spsi, k, cx, cy, Fx, Fy);
+            force_at<real, SH>(L, srho, spsi, k, cx, cy, Fx, Fy);
             first_moment<real>(fk, jx, jy);   // FP32: the reference density adds no momentum
             r[k] = (double)srho[k][cy][cx];
             m[k][0] = (double)(jx + (real)0.5 * Fx);

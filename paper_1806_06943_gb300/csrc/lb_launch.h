@@ -10,11 +10,20 @@ namespace lbk {
 
 template <typename real>
 struct Launch {
-    // one kernel launch over tiles [tile_offset, tile_offset + n_tiles)
+    // one kernel launch over tiles [tile_offset, tile_offset + n_tiles) of
+    // height ty (2, 4 or 8)
     static cudaError_t density(const Lat<real> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
-                               cudaStream_t s);
+                               int ty, cudaStream_t s);
     static cudaError_t collide(const Lat<real> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
-                               cudaStream_t s);
+                               int ty, cudaStream_t s);
+    // nsteps time steps of all tiles in one persistent launch of `blocks`
+    // blocks (ctl, dens_done, coll_done cleared by the caller beforehand)
+    static cudaError_t persistent(const Lat<real> *lats, const int4 *tiles, const int *lat_ntiles, int n_tiles,
+                                  int nsteps, int parity0,
+                                  void *ctl, unsigned *dens_done, unsigned *coll_done, int *err, long long wait_cycles,
+                                  int drop_tile, int ty, int blocks, cudaStream_t s);
+    // resident blocks per SM of the persistent kernel for tile height ty
+    static int persistent_blocks_per_sm(int ty);
     static cudaError_t observe(const Lat<real> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
                                double *partials, double *rho, double *mom, double *ubar, cudaStream_t s);
     static cudaError_t finalize(const Lat<real> *lats, int n_lat, const double *partials, double *obs, cudaStream_t s);

@@ -9,20 +9,71 @@ namespace lbk {
 
 template <typename real>
 cudaError_t Launch<real>::density(const Lat<real> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
-                                  cudaStream_t s)
+                                  int ty, cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaSuccess;
-    k_density<real><<<n_tiles, dim3(TX, TY), 0, s>>>(lats, tiles, tile_offset, parity);
+    switch (ty) {
+    case 2: k_density<real, 2><<<n_tiles, dim3(TX, 2), 0, s>>>(lats, tiles, tile_offset, parity); break;
+    case 4: k_density<real, 4><<<n_tiles, dim3(TX, 4), 0, s>>>(lats, tiles, tile_offset, parity); break;
+    case 8: k_density<real, 8><<<n_tiles, dim3(TX, 8), 0, s>>>(lats, tiles, tile_offset, parity); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t Launch<real>::collide(const Lat<real> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
-                                  cudaStream_t s)
+                                  int ty, cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaSuccess;
-    k_collide<real><<<n_tiles, dim3(TX, TY), 0, s>>>(lats, tiles, tile_offset, parity);
+    switch (ty) {
+    case 2: k_collide<real, 2><<<n_tiles, dim3(TX, 2), 0, s>>>(lats, tiles, tile_offset, parity); break;
+    case 4: k_collide<real, 4><<<n_tiles, dim3(TX, 4), 0, s>>>(lats, tiles, tile_offset, parity); break;
+    case 8: k_collide<real, 8><<<n_tiles, dim3(TX, 8), 0, s>>>(lats, tiles, tile_offset, parity); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t Launch<real>::persistent(const Lat<real> *lats, const int4 *tiles, const int *lat_ntiles, int n_tiles,
+                                     int nsteps, int parity0,
+                                     void *ctl, unsigned *dens_done, unsigned *coll_done, int *err,
+                                     long long wait_cycles, int drop_tile, int ty, int blocks, cudaStream_t s)
+{
+    if (n_tiles <= 0 || nsteps <= 0) return cudaSuccess;
+    PersistCtl *c = (PersistCtl *)ctl;
+    switch (ty) {
+    case 2:
+        k_persistent<real, 2><<<blocks, dim3(TX, 2), 0, s>>>(lats, tiles, lat_ntiles, n_tiles, nsteps, parity0, c, dens_done,
+                                                              coll_done, err, wait_cycles, drop_tile);
+        break;
+    case 4:
+        k_persistent<real, 4><<<blocks, dim3(TX, 4), 0, s>>>(lats, tiles, lat_ntiles, n_tiles, nsteps, parity0, c, dens_done,
+                                                              coll_done, err, wait_cycles, drop_tile);
+        break;
+    case 8:
+        k_persistent<real, 8><<<blocks, dim3(TX, 8), 0, s>>>(lats, tiles, lat_ntiles, n_tiles, nsteps, parity0, c, dens_done,
+                                                              coll_done, err, wait_cycles, drop_tile);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename real>
+int Launch<real>::persistent_blocks_per_sm(int ty)
+{
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (ty == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<real, 2>, TX * 2, 0);
+    if (ty == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<real, 4>, TX * 4, 0);
+    if (ty == 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<real, 8>, TX * 8, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 template <typename real>

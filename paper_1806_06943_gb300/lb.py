@@ -24,6 +24,7 @@ LB_FP64, LB_FP32 = 0, 1
 LB_PERIODIC, LB_WALLS_Y = 0, 1
 LB_WALL_MIRROR, LB_WALL_FIXED = 0, 1
 LB_STATIC_MAX_TILES = 32768
+LB_MODE_LAUNCH, LB_MODE_PERSISTENT = 0, 1
 
 
 class LBError(RuntimeError):
@@ -89,6 +90,9 @@ SIGNATURES = {
     "lb_save": (ctypes.c_int, [_vp, _vp, _P(_sz)]),
     "lb_load": (ctypes.c_int, [_vp, _vp, _sz]),
     "lb_profile": (ctypes.c_int, [_vp, _i32, _vp, _sz, _dp]),
+    "lb_set_config": (ctypes.c_int, [_vp, _i32, _i32]),
+    "lb_get_config": (ctypes.c_int, [_vp, _P(_i32), _P(_i32)]),
+    "lb_autotune": (ctypes.c_int, [_vp, _i32, ctypes.c_char_p, _dp]),
     "lb_batch_create": (ctypes.c_int, [_P(lb_params), _i32, _P(_vp)]),
     "lb_batch_destroy": (None, [_vp]),
     "lb_batch_size": (ctypes.c_int, [_vp]),
@@ -99,6 +103,10 @@ SIGNATURES = {
     "lb_batch_observables": (ctypes.c_int, [_vp, _P(lb_obs)]),
     "lb_batch_get_fields": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
     "lb_batch_profile": (ctypes.c_int, [_vp, _i32, _vp, _sz, _dp]),
+    "lb_batch_set_config": (ctypes.c_int, [_vp, _i32, _i32]),
+    "lb_batch_get_config": (ctypes.c_int, [_vp, _P(_i32), _P(_i32)]),
+    "lb_batch_autotune": (ctypes.c_int, [_vp, _i32, ctypes.c_char_p, _dp]),
+    "lb_batch_set_wait_limit": (ctypes.c_int, [_vp, _d, _i32]),
     "lb_observables_static": (ctypes.c_int, [_P(lb_params), _vp, _d, _d, _d, _vp]),
 }
 
@@ -244,6 +252,20 @@ class Lattice:
         _check(LIB.lb_profile(self.h, int(nsteps), flush_ptr, int(flush_bytes), ms))
         return tuple(ms)
 
+    def set_config(self, mode: int, tile_height: int):
+        _check(LIB.lb_set_config(self.h, int(mode), int(tile_height)))
+
+    def config(self) -> tuple:
+        m, t = ctypes.c_int32(), ctypes.c_int32()
+        _check(LIB.lb_get_config(self.h, ctypes.byref(m), ctypes.byref(t)))
+        return m.value, t.value
+
+    def autotune(self, trial_steps: int = 64, cache_path: str | None = None) -> float:
+        ms = ctypes.c_double()
+        _check(LIB.lb_autotune(self.h, int(trial_steps), cache_path.encode() if cache_path else None,
+                               ctypes.byref(ms)))
+        return ms.value
+
     def save(self) -> bytes:
         n = ctypes.c_size_t(0)
         _check(LIB.lb_save(self.h, None, ctypes.byref(n)))
@@ -309,6 +331,23 @@ class Batch:
         ms = (ctypes.c_double * 3)()
         _check(LIB.lb_batch_profile(self.b, int(nsteps), flush_ptr, int(flush_bytes), ms))
         return tuple(ms)
+
+    def set_config(self, mode: int, tile_height: int):
+        _check(LIB.lb_batch_set_config(self.b, int(mode), int(tile_height)))
+
+    def config(self) -> tuple:
+        m, t = ctypes.c_int32(), ctypes.c_int32()
+        _check(LIB.lb_batch_get_config(self.b, ctypes.byref(m), ctypes.byref(t)))
+        return m.value, t.value
+
+    def autotune(self, trial_steps: int = 64, cache_path: str | None = None) -> float:
+        ms = ctypes.c_double()
+        _check(LIB.lb_batch_autotune(self.b, int(trial_steps), cache_path.encode() if cache_path else None,
+                                     ctypes.byref(ms)))
+        return ms.value
+
+    def set_wait_limit(self, seconds: float, drop_tile: int = -1):
+        _check(LIB.lb_batch_set_wait_limit(self.b, float(seconds), int(drop_tile)))
 
     def fields(self, i) -> dict:
         n = self.shapes[i]
