@@ -224,6 +224,22 @@ int lb_load(lb_handle *h, const void *buf, size_t len);
  * nsteps.  Synchronises. */
 int lb_profile(lb_handle *h, int32_t nsteps, void *flush_buf, size_t flush_bytes, double ms[3]);
 
+/* Objectives of lb_grad. */
+#define LB_OBJ_MU_R 0     /* relative effective viscosity mu_r = Q0 / Q (walls, g_x != 0) */
+#define LB_OBJ_DP 1       /* Laplace pressure jump dp_laplace around the probe */
+
+/* Gradient of an observable J of the state reached after nsteps time steps,
+ * with respect to theta = (G_AB, G1, G2, tau_A, tau_B), by the discrete
+ * adjoint of the time step (reverse of Eqs. 1-3, 5, 6, 8, 9 with streaming and
+ * bounce-back): a forward sweep stores the populations every ckpt_every steps;
+ * each segment is then recomputed from its checkpoint and stepped backwards.
+ * On return the lattice holds the state after nsteps steps (as lb_step would
+ * leave it), *J the observable there and dJ[5] its gradient; parameter
+ * gradients are accumulated in FP64.  Needs an LB_FP64 lattice; LB_OBJ_DP
+ * needs a probe.  Device memory: (nsteps/ckpt_every + ckpt_every + 3) copies of
+ * the populations plus 22 planes, allocated for the call.  Synchronises. */
+int lb_grad(lb_handle *h, int64_t nsteps, int32_t ckpt_every, int32_t objective, double *J, double dJ[5]);
+
 /* ---- many independent lattices advanced together ------------------------- */
 
 /* Create n >= 1 lattices of possibly different sizes and parameters that

@@ -30,6 +30,7 @@ UNITS = {
     "lb_fp64.cu": ["-fmad=false"],
     "lb_fp32.cu": [],
     "lb_noalloc.cu": ["-fmad=false"],
+    "lb_adjoint.cu": ["-fmad=false"],
 }
 
 

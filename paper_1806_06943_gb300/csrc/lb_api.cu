@@ -508,6 +508,123 @@ struct lb_engine {
         return end();
     }
 
+    // Gradient of an observable of the state after nsteps steps with respect
+    // to (G_AB, G1, G2, tau_A, tau_B), by the discrete adjoint with a
+    // checkpoint every ckpt steps and recomputation of each segment.
+    int grad(int64_t nsteps, int ckpt, int objective, double *J, double dJ[5])
+    {
+        if (precision != LB_FP64) return fail(LB_EINVAL, "lb_grad needs an LB_FP64 lattice");
+        if (nsteps < 1 || ckpt < 1) return fail(LB_EINVAL, "lb_grad needs nsteps >= 1 and ckpt_every >= 1");
+        if (!J || !dJ) return fail(LB_EINVAL, "J and dJ must not be NULL");
+        const lb_params &p = P[0];
+        lbk::Lat<double> L = L64[0];
+        if (objective == LB_OBJ_MU_R) {
+            if (!p.walls || p.g[0] == 0.0) return fail(LB_EINVAL, "mu_r needs walls and a body force g_x");
+        } else if (objective == LB_OBJ_DP) {
+            if (!L.has_probe) return fail(LB_EINVAL, "the Laplace objective needs a probe (lb_set_probe)");
+        } else {
+            return fail(LB_EINVAL, "objective must be LB_OBJ_MU_R or LB_OBJ_DP");
+        }
+        int rc = begin();
+        if (rc) return rc;
+        const size_t pop = pop_bytes(0), plane_b = plane(0) * sizeof(double);
+        const int64_t nseg = (nsteps + ckpt - 1) / ckpt;
+        const int seg_len = (int)std::min<int64_t>(ckpt, nsteps);
+        const int tiles_x = (p.nx + lbk::TX - 1) / lbk::TX, tiles_y = (p.ny + lbk::TY - 1) / lbk::TY;
+        const int ntl = tiles_x * tiles_y;
+        char *mem = nullptr;
+        const size_t bytes = (size_t)nseg * pop + (size_t)seg_len * pop + 3 * pop + lbk::kAdjSlotCount * plane_b +
+                             2 * plane_b + (size_t)ntl * 8 * sizeof(double) + 8 * sizeof(double);
+        if (cudaMalloc((void **)&mem, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LB_ENOMEM, "lb_grad: no room for checkpoints and adjoint buffers");
+        }
+        char *q = mem;
+        auto take = [&](size_t b) { char *r = q; q += b; return r; };
+        char *ckpts = take((size_t)nseg * pop), *seg = take((size_t)seg_len * pop);
+        double *lam[2] = {(double *)take(pop), (double *)take(pop)};
+        char *final_state = take(pop);
+        double *abuf = (double *)take(lbk::kAdjSlotCount * plane_b), *rho = (double *)take(2 * plane_b);
+        double *gpart = (double *)take((size_t)ntl * 8 * sizeof(double)), *gout = (double *)take(8 * sizeof(double));
+        cudaError_t ce = cudaMemsetAsync(gpart, 0, (size_t)ntl * 8 * sizeof(double), stream);
+        auto done = [&](int code) {
+            cudaStreamSynchronize(stream);
+            cudaFree(mem);
+            return code;
+        };
+        // forward sweep, keeping a checkpoint at the start of every segment
+        for (int64_t s = 0; s < nseg && ce == cudaSuccess; ++s) {
+            ce = cudaMemcpyAsync(ckpts + s * pop, fbuf(0, parity), pop, cudaMemcpyDeviceToDevice, stream);
+            if (ce == cudaSuccess && (rc = step(std::min<int64_t>(ckpt, nsteps - s * ckpt)))) return done(rc);
+        }
+        if (ce != cudaSuccess) return done(cuda_fail(ce, "lb_grad forward sweep"));
+        lb_obs o;
+        if ((rc = observables(&o))) return done(rc);
+        double seed_a = 0.0, seed_b = 0.0;
+        const int kind = objective == LB_OBJ_MU_R ? 1 : 2;
+        if (objective == LB_OBJ_MU_R) {
+            *J = o.mu_r;
+            seed_a = -o.mu_r / o.flux_Q;   // d(Q0/Q)/dQ
+        } else {
+            *J = o.dp_laplace;
+            double nin = 0, nout = 0;
+            for (int y = 0; y < p.ny; ++y)
+                for (int x = 0; x < p.nx; ++x) {
+                    double dx = std::fabs(x - L.probe[0]), dy = std::fabs(y - L.probe[1]);
+                    if (dx > 0.5 * p.nx) dx = p.nx - dx;
+                    if (!p.walls && dy > 0.5 * p.ny) dy = p.ny - dy;
+                    const double rr = std::sqrt(dx * dx + dy * dy);
+                    if (rr < 0.5 * L.probe[2]) nin += 1;
+                    if (rr > L.probe[2] + 6.0) nout += 1;
+                }
+            seed_a = 1.0 / nin;
+            seed_b = -1.0 / nout;
+        }
+        const int par_final = parity;
+        ce = cudaMemcpyAsync(final_state, fbuf(0, par_final), pop, cudaMemcpyDeviceToDevice, stream);
+        // seed: lam(T) = dJ/df(T)
+        const double *fT = (const double *)fbuf(0, par_final);
+        if (ce == cudaSuccess) ce = lbk::adj_density(L, fT, rho, stream);
+        if (ce == cudaSuccess) ce = lbk::adj_step(L, fT, rho, nullptr, abuf, gpart, lam[0], kind, seed_a, seed_b, stream);
+        int cur = 0;
+        // backward over the segments, recomputing each from its checkpoint
+        for (int64_t s = nseg - 1; s >= 0 && ce == cudaSuccess; --s) {
+            const int len = (int)std::min<int64_t>(ckpt, nsteps - s * ckpt);
+            ce = cudaMemcpyAsync(seg, ckpts + s * pop, pop, cudaMemcpyDeviceToDevice, stream);
+            for (int j = 1; j < len && ce == cudaSuccess; ++j) {
+                ce = cudaMemcpyAsync(fbuf(0, 0), seg + (size_t)(j - 1) * pop, pop, cudaMemcpyDeviceToDevice, stream);
+                if (ce == cudaSuccess) ce = launch_step(0);
+                if (ce == cudaSuccess)
+                    ce = cudaMemcpyAsync(seg + (size_t)j * pop, fbuf(0, 1), pop, cudaMemcpyDeviceToDevice, stream);
+            }
+            for (int j = len - 1; j >= 0 && ce == cudaSuccess; --j) {
+                const double *ft = (const double *)(seg + (size_t)j * pop);
+                ce = lbk::adj_density(L, ft, rho, stream);
+                if (ce == cudaSuccess)
+                    ce = lbk::adj_step(L, ft, rho, lam[cur], abuf, gpart, lam[cur ^ 1], 0, 0.0, 0.0, stream);
+                cur ^= 1;
+            }
+        }
+        if (ce == cudaSuccess) ce = lbk::adj_reduce(gpart, ntl, gout, stream);
+        double g[8] = {0};
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(g, gout, 8 * sizeof(double), cudaMemcpyDeviceToHost, stream);
+        // put the final state back (the recomputation used both population copies)
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(fbuf(0, 0), final_state, pop, cudaMemcpyDeviceToDevice, stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+        if (ce != cudaSuccess) return done(cuda_fail(ce, "lb_grad adjoint sweep"));
+        parity = 0;
+        drop_graph();
+        // theta = (G_AB, G1, G2, tau_A, tau_B); d omega / d tau = -omega^2
+        dJ[0] = g[0];
+        dJ[1] = g[1];
+        dJ[2] = g[2];
+        dJ[3] = -g[3] * L.omega[0] * L.omega[0];
+        dJ[4] = -g[4] * L.omega[1] * L.omega[1];
+        if (objective == LB_OBJ_MU_R) dJ[4] += -o.mu_r / (3.0 * ((p.tau[1] - 0.5) / 3.0));   // Q0(tau_B)
+        (void)par_final;
+        return done(end());
+    }
+
     int observables(lb_obs *o)
     {
         int rc = begin();
@@ -978,6 +1095,12 @@ int lb_profile(lb_handle *h, int32_t nsteps, void *flush_buf, size_t flush_bytes
 {
     CHECK_H(h);
     return h->e->profile(nsteps, flush_buf, flush_bytes, ms);
+}
+
+int lb_grad(lb_handle *h, int64_t nsteps, int32_t ckpt_every, int32_t objective, double *J, double dJ[5])
+{
+    CHECK_H(h);
+    return h->e->grad(nsteps, ckpt_every, objective, J, dJ);
 }
 
 int lb_batch_create(const lb_params *p, int32_t n, lb_batch **out)

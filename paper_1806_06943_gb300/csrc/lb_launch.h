@@ -38,6 +38,17 @@ struct Launch {
 extern template struct Launch<double>;
 extern template struct Launch<float>;
 
+// Discrete adjoint of the FP64 step (lb_adjoint.cu).  Buffers use the
+// lattice's pitched layout; abuf holds 20 planes, gpart 8 doubles per tile of
+// 32 x 4 nodes.  seed_kind: 0 adjoint step (lam_next = dJ/df(t+1)), 1 seed of
+// mu_r (seed_a = dJ/dQ), 2 seed of the Laplace pressure jump (seed_a = 1/n_in,
+// seed_b = -1/n_out, probe in L).
+cudaError_t adj_density(const Lat<double> &L, const double *f, double *rho, cudaStream_t s);
+cudaError_t adj_step(const Lat<double> &L, const double *f, const double *rho, const double *lam_next, double *abuf,
+                     double *gpart, double *lam_out, int seed_kind, double seed_a, double seed_b, cudaStream_t s);
+cudaError_t adj_reduce(const double *gpart, int n_tiles, double *out, cudaStream_t s);
+constexpr int kAdjSlotCount = 20;
+
 // Record msg as the calling thread's lb_last_error() message.
 void set_last_error(const char *msg);
 

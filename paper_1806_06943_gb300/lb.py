@@ -25,6 +25,7 @@ LB_PERIODIC, LB_WALLS_Y = 0, 1
 LB_WALL_MIRROR, LB_WALL_FIXED = 0, 1
 LB_STATIC_MAX_TILES = 32768
 LB_MODE_LAUNCH, LB_MODE_PERSISTENT = 0, 1
+LB_OBJ_MU_R, LB_OBJ_DP = 0, 1
 
 
 class LBError(RuntimeError):
@@ -90,6 +91,7 @@ SIGNATURES = {
     "lb_save": (ctypes.c_int, [_vp, _vp, _P(_sz)]),
     "lb_load": (ctypes.c_int, [_vp, _vp, _sz]),
     "lb_profile": (ctypes.c_int, [_vp, _i32, _vp, _sz, _dp]),
+    "lb_grad": (ctypes.c_int, [_vp, _i64, _i32, _i32, _dp, _dp]),
     "lb_set_config": (ctypes.c_int, [_vp, _i32, _i32]),
     "lb_get_config": (ctypes.c_int, [_vp, _P(_i32), _P(_i32)]),
     "lb_autotune": (ctypes.c_int, [_vp, _i32, ctypes.c_char_p, _dp]),
@@ -251,6 +253,13 @@ class Lattice:
         ms = (ctypes.c_double * 3)()
         _check(LIB.lb_profile(self.h, int(nsteps), flush_ptr, int(flush_bytes), ms))
         return tuple(ms)
+
+    def grad(self, nsteps: int, ckpt_every: int, objective: int = LB_OBJ_MU_R):
+        """(J, dJ/d(G_AB, G1, G2, tau_A, tau_B)) after nsteps steps from the current state."""
+        J = ctypes.c_double()
+        dJ = (ctypes.c_double * 5)()
+        _check(LIB.lb_grad(self.h, int(nsteps), int(ckpt_every), int(objective), ctypes.byref(J), dJ))
+        return J.value, np.array(list(dJ))
 
     def set_config(self, mode: int, tile_height: int):
         _check(LIB.lb_set_config(self.h, int(mode), int(tile_height)))

@@ -1,0 +1,103 @@
+"""The hand-written discrete adjoint (lb_grad) against central finite
+differences of the FP64 oracle (h = 1e-4), for the relative effective
+viscosity of a body-forced channel and the Laplace pressure jump of a drop,
+and through torch.autograd.  Tolerance: 1e-4 relative, normwise over the five
+parameters (G_AB, G1, G2, tau_A, tau_B)."""
+import numpy as np
+import pytest
+
+from paper_1806_06943_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+THETA0 = np.array([3.0, -7.4, 6.4, 1.5, 1.0])
+
+
+@pytest.fixture(scope="module")
+def lbmod():
+    from paper_1806_06943_gb300 import build
+    build.build()
+    from paper_1806_06943_gb300 import lb
+    return lb
+
+
+def oracle_J(oracle_mod, theta, rho, nsteps, objective, probe=None, **kw):
+    o = oracle_mod.OracleSim(rho.shape[2], rho.shape[1], G_AB=theta[0], G1=theta[1], G2=theta[2],
+                             tau=(theta[3], theta[4]), **kw)
+    o.set_fields(rho)
+    o.step(nsteps)
+    obs = o.observables(probe or (0.0, 0.0, 0.0))
+    return obs["mu_r"] if objective == 0 else obs["dp"]
+
+
+def fd_grad(oracle_mod, theta, rho, nsteps, objective, h=1e-4, **kw):
+    g = np.zeros(5)
+    for a in range(5):
+        tp, tm = theta.copy(), theta.copy()
+        tp[a] += h
+        tm[a] -= h
+        g[a] = (oracle_J(oracle_mod, tp, rho, nsteps, objective, **kw)
+                - oracle_J(oracle_mod, tm, rho, nsteps, objective, **kw)) / (2 * h)
+    return g
+
+
+def channel_case():
+    nx, ny = 32, 20
+    rho = W.droplet(nx, ny, 5.0, cx=15.5, cy=9.5, seed=41, periodic=False)
+    kw = dict(g=(1e-5, 0.0), walls=1, wall_mode=1, wall_rho=(0.03, 1.0))
+    return nx, ny, rho, kw
+
+
+def test_mu_r_gradient_matches_oracle_fd(lbmod, oracle_mod):
+    nx, ny, rho, kw = channel_case()
+    nsteps = 120
+    L = lbmod.Lattice(nx, ny, G_AB=THETA0[0], G1=THETA0[1], G2=THETA0[2], tau=(THETA0[3], THETA0[4]), **kw)
+    L.set_fields(rho)
+    J, dJ = L.grad(nsteps, 25, lbmod.LB_OBJ_MU_R)
+    J0 = oracle_J(oracle_mod, THETA0, rho, nsteps, 0, **kw)
+    assert abs(J - J0) <= 1e-12 * abs(J0)
+    g = fd_grad(oracle_mod, THETA0, rho, nsteps, 0, **kw)
+    assert np.max(np.abs(dJ - g)) <= 1e-4 * np.max(np.abs(g)), (dJ, g)
+    # the lattice is left where lb_step would leave it
+    M = lbmod.Lattice(nx, ny, G_AB=THETA0[0], G1=THETA0[1], G2=THETA0[2], tau=(THETA0[3], THETA0[4]), **kw)
+    M.set_fields(rho)
+    M.step(nsteps)
+    assert L.t == nsteps and np.array_equal(L.get_populations(), M.get_populations())
+
+
+def test_laplace_gradient_matches_oracle_fd(lbmod, oracle_mod):
+    n = 32
+    rho = W.droplet(n, n, 8.0, seed=42)
+    probe = (n / 2, n / 2, 8.0)
+    theta = np.array([3.0, -7.4, 6.4, 1.0, 1.2])
+    nsteps = 80
+    L = lbmod.Lattice(n, n, G_AB=theta[0], G1=theta[1], G2=theta[2], tau=(theta[3], theta[4]))
+    L.set_fields(rho)
+    L.set_probe(*probe)
+    J, dJ = L.grad(nsteps, 30, lbmod.LB_OBJ_DP)
+    assert abs(J - oracle_J(oracle_mod, theta, rho, nsteps, 1, probe=probe)) <= 1e-10 * abs(J)
+    g = fd_grad(oracle_mod, theta, rho, nsteps, 1, probe=probe)
+    assert np.max(np.abs(dJ - g)) <= 1e-4 * np.max(np.abs(g)), (dJ, g)
+
+
+def test_autograd_function(lbmod, oracle_mod):
+    torch = pytest.importorskip("torch")
+    from paper_1806_06943_gb300.autograd import observable
+    nx, ny, rho, kw = channel_case()
+    spec = dict(nx=nx, ny=ny, rho=rho, nsteps=60, ckpt_every=16, objective=lbmod.LB_OBJ_MU_R, **kw)
+    theta = torch.tensor(THETA0, dtype=torch.float64, requires_grad=True)
+    J = observable(theta, spec)
+    (2.0 * J).backward()
+    g = fd_grad(oracle_mod, THETA0, rho, 60, 0, **kw)
+    assert np.max(np.abs(theta.grad.numpy() - 2.0 * g)) <= 2e-4 * np.max(np.abs(g))
+
+
+def test_rejects_unsupported(lbmod):
+    L = lbmod.Lattice(16, 16, precision=lbmod.LB_FP32)
+    with pytest.raises(lbmod.LBError):
+        L.grad(10, 5, lbmod.LB_OBJ_DP)
+    P = lbmod.Lattice(16, 16)
+    with pytest.raises(lbmod.LBError):   # periodic: no mu_r
+        P.grad(10, 5, lbmod.LB_OBJ_MU_R)
+    with pytest.raises(lbmod.LBError):   # no probe
+        P.grad(10, 5, lbmod.LB_OBJ_DP)
