@@ -178,6 +178,23 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_traffic(workload: str):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary
+    (profiles/k_collide_traffic.json), if it was taken on this workload and on
+    the current kernel source; else None."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_collide_traffic.json")) as f:
+            d = json.load(f)
+        src = os.path.join(ROOT, "paper_1806_06943_gb300", "csrc", "lb_kernels.cuh")
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        if d.get("workload") == workload and d.get("kernel_source_sha1") == sha:
+            return float(d["bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -319,7 +336,8 @@ def main():
         "roofline": {
             "bound": "hbm", "kernel": f"k_collide<{'float' if prec else 'double'}> (fused force+collide+stream)",
             "achieved": BYTES_COLLIDE[prec] * sites / (ms[1] * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-            "frac": BYTES_COLLIDE[prec] * sites / (ms[1] * 1e-3) / 1e9 / peak, "traffic": None,
+            "frac": BYTES_COLLIDE[prec] * sites / (ms[1] * 1e-3) / 1e9 / peak,
+            "traffic": kernel_traffic(args.workload) if prec == lb.LB_FP32 else None,
             "peak_source": f"{peak_kind} hbm_gbs (burst)",
             "algorithmic_bytes_per_site": BYTES_COLLIDE[prec], "units_per_launch": sites,
             "ms_per_launch": ms[1],
@@ -341,6 +359,18 @@ def main():
             ev1.record(stream)
         ev1.synchronize()
         out["graph_sustained_mlups"] = sites * 256 / (ev0.elapsed_time(ev1) * 1e-3) / 1e6
+
+        # autotuned execution configuration (mode, tile height) and its sustained rate
+        tuned_ms = b.autotune(64, None)
+        mode, tyh = b.config()
+        b.synchronize()
+        ev0.record(stream)
+        b.step(256)
+        ev1.record(stream)
+        ev1.synchronize()
+        out["autotuned"] = {"mode": ["launch", "persistent"][mode], "tile_height": tyh,
+                            "trial_ms_per_step": tuned_ms,
+                            "sustained_mlups": sites * 256 / (ev0.elapsed_time(ev1) * 1e-3) / 1e6}
 
         # Laplace fit at ratio 1 after the run so far (not converged; sanity only)
         # FP64 on the same batch
@@ -401,6 +431,23 @@ def main():
                       "step": f"upload fields of all 24 lattices + {S} time steps + observables readback"}
         out["gpu_launches"] = gpu_launches
         del be
+
+        # adjoint: gradient of mu_r for the 512 x 128 channel emulsion, 5000
+        # steps, checkpoints every 250 (FP64 forward, recomputation, adjoint)
+        from paper_1806_06943_gb300 import workloads as W
+        rho_c, _, _, phi_c = W.hex_emulsion(512, 128, 0.5, R=12.0, spread=2.0, gap=3.0, walls=True,
+                                            seed=W.BASE_SEED + 3)
+        Lc = lb.Lattice(512, 128, tau=(1.0, 1.0), g=(1e-6, 0.0), walls=1, wall_mode=1, wall_rho=(0.03, 1.0),
+                        stream=sptr, **C6)
+        Lc.set_fields(rho_c)
+        t0 = time.perf_counter()
+        Jc, dJc = Lc.grad(5000, 250, lb.LB_OBJ_MU_R)
+        tg = time.perf_counter() - t0
+        out["adjoint_channel_512x128"] = {"steps": 5000, "ckpt_every": 250, "phi_achieved": phi_c, "mu_r": Jc,
+                                          "dmu_r_dtheta": [float(v) for v in dJc],
+                                          "theta": "G_AB, G1, G2, tau_A, tau_B", "seconds": tg,
+                                          "forward_equivalent_mlups": 512 * 128 * 5000 / tg / 1e6}
+        del Lc
 
         # CPU oracle on a bounded sample (rank 0 only)
         if rank == 0 and world == 1:
