@@ -117,3 +117,32 @@ def test_long_wave_force_matches_bulk_eos(oracle_mod, G_AB, G1, G2):
     dp = np.real(np.fft.ifft(1j * kk * np.fft.fft(pnon)))
     err = np.max(np.abs(Fx + dp)) / np.max(np.abs(dp))
     assert err < 2e-3, err
+
+
+def test_mirror_walls_equal_reflected_periodic_lattice(oracle_mod):
+    """Mirrored ghost rows (neutral walls) are the reflection of the fluid
+    about y = -1/2 and y = ny - 1/2: the forces at every fluid row equal those
+    of a periodic lattice twice as high holding the reflected field."""
+    rng = np.random.default_rng(8)
+    nx, ny = 12, 8
+    rho = 0.3 + 0.6 * rng.random((2, ny, nx))
+    Fw = _forces(oracle_mod, rho, walls=1, wall_mode=0, **dict(G_AB=3.0, G1=-7.4, G2=6.4))
+    big = np.concatenate([rho, rho[:, ::-1, :]], axis=1)       # rows ny..2ny-1 reflected
+    Fp = _forces(oracle_mod, big, **dict(G_AB=3.0, G1=-7.4, G2=6.4))
+    assert np.array_equal(Fw, Fp[:, :, :ny, :])
+
+
+def test_fixed_walls_equal_periodic_lattice_with_wall_rows(oracle_mod):
+    """Fixed ghost rows (non-wetting walls) act like two rows of the wall
+    densities on each side of a periodic lattice."""
+    rng = np.random.default_rng(9)
+    nx, ny = 12, 8
+    rho = 0.3 + 0.6 * rng.random((2, ny, nx))
+    wall = (0.03, 1.0)
+    Fw = _forces(oracle_mod, rho, walls=1, wall_mode=1, wall_rho=wall, **dict(G_AB=3.0, G1=-7.4, G2=6.4))
+    pad = np.empty((2, 4, nx))
+    pad[0], pad[1] = wall
+    big = np.concatenate([rho, pad], axis=1)
+    Fp = _forces(oracle_mod, big, **dict(G_AB=3.0, G1=-7.4, G2=6.4))
+    # the padded rows hold sum_i f^eq(0.03) rather than 0.03 itself: rounding only
+    assert np.max(np.abs(Fw - Fp[:, :, :ny, :])) < 1e-15
