@@ -36,8 +36,10 @@ sys.path.insert(0, ROOT)
 
 C6 = dict(G_AB=3.0, G1=-7.4, G2=6.4)
 FLUSH_BYTES = 256 << 20
-BYTES_COLLIDE = {1: 152, 0: 304}   # algorithmic bytes / site: 18 pops read + 18 written + 2 rho read
-BYTES_DENSITY = {1: 88, 0: 160}    # 18 pops read + 2 rho written (+ 2 reference rho read in FP32)
+# algorithmic bytes per node and launch (FP32 offset / FP64 plain):
+BYTES_FUSED = {1: 160, 0: 288}     # one-pass: 18 pops read + 18 written (+ 2 reference rho read, 2 written)
+BYTES_COLLIDE = {1: 152, 0: 304}   # two-pass fused kernel: 18 pops read + 18 written + 2 rho read
+BYTES_DENSITY = {1: 88, 0: 160}    # density pass: 18 pops read + 2 rho written (+ 2 reference rho read)
 
 
 def parse():
@@ -51,6 +53,8 @@ def parse():
                     choices=["laplace_sweep_24", "dense_emulsion_4096", "dense_emulsion_2048"],
                     help="main-leg workload (the dense emulsions are single periodic lattices)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--mode", default="fused", choices=["fused", "launch"],
+                    help="time step as one pass (fused) or density pass + fused kernel (launch)")
     return ap.parse_args()
 
 
@@ -178,7 +182,7 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_traffic(workload: str):
+def kernel_traffic(workload: str, kernel: str):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary
     (profiles/k_collide_traffic.json), if it was taken on this workload and on
     the current kernel source; else None."""
@@ -188,7 +192,7 @@ def kernel_traffic(workload: str):
             d = json.load(f)
         src = os.path.join(ROOT, "paper_1806_06943_gb300", "csrc", "lb_kernels.cuh")
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-        if d.get("workload") == workload and d.get("kernel_source_sha1") == sha:
+        if d.get("workload") == workload and d.get("kernel") == kernel and d.get("kernel_source_sha1") == sha:
             return float(d["bytes_per_launch"])
     except Exception:
         pass
@@ -295,6 +299,10 @@ def main():
     sites = sum(s["nx"] * s["ny"] for s in specs)
     prec = lb.LB_FP32 if args.precision == "fp32" else lb.LB_FP64
     b = make_batch(lb, specs, fields, prec, sptr)
+    mode = lb.LB_MODE_FUSED if args.mode == "fused" else lb.LB_MODE_LAUNCH
+    b.set_config(mode, 4)
+    kbytes = BYTES_FUSED if mode == lb.LB_MODE_FUSED else BYTES_COLLIDE
+    kname = ("k_fused" if mode == lb.LB_MODE_FUSED else "k_collide") + f"<{'float' if prec else 'double'}, 4>"
 
     # warm-up (untimed), then the timed region: K steps, barrier + sync on both sides
     b.profile(args.warmup, flush.data_ptr(), FLUSH_BYTES)
@@ -334,16 +342,15 @@ def main():
         "clocks": clk,
         "gpu_launches": gpu_launches,
         "roofline": {
-            "bound": "hbm", "kernel": f"k_collide<{'float' if prec else 'double'}> (fused force+collide+stream)",
-            "achieved": BYTES_COLLIDE[prec] * sites / (ms[1] * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-            "frac": BYTES_COLLIDE[prec] * sites / (ms[1] * 1e-3) / 1e9 / peak,
-            "traffic": kernel_traffic(args.workload) if prec == lb.LB_FP32 else None,
+            "bound": "hbm", "kernel": kname,
+            "achieved": kbytes[prec] * sites / (ms[1] * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": kbytes[prec] * sites / (ms[1] * 1e-3) / 1e9 / peak,
+            "traffic": kernel_traffic(args.workload, kname) if prec == lb.LB_FP32 else None,
             "peak_source": f"{peak_kind} hbm_gbs (burst)",
-            "algorithmic_bytes_per_site": BYTES_COLLIDE[prec], "units_per_launch": sites,
+            "algorithmic_bytes_per_site": kbytes[prec], "units_per_launch": sites,
             "ms_per_launch": ms[1],
         },
-        "density_pass": {"ms_per_launch": ms[0], "algorithmic_bytes_per_site": BYTES_DENSITY[prec],
-                         "achieved_gbs": BYTES_DENSITY[prec] * sites / (ms[0] * 1e-3) / 1e9},
+        "mode": args.mode,
         "wall_s_timed": t_wall,
         "observables_after": {"finite": all(o["finite"] == 1.0 for o in obs),
                               "gamma_fit_ratio1": None},
@@ -360,28 +367,38 @@ def main():
         ev1.synchronize()
         out["graph_sustained_mlups"] = sites * 256 / (ev0.elapsed_time(ev1) * 1e-3) / 1e6
 
+        # two-pass breakdown of the same batch: density pass + fused kernel
+        b.set_config(lb.LB_MODE_LAUNCH, 4)
+        b.profile(3, flush.data_ptr(), FLUSH_BYTES)
+        m2 = b.profile(max(20, args.steps // 2), flush.data_ptr(), FLUSH_BYTES)
+        out["two_pass"] = {"mlups": sites / (m2[2] * 1e-3) / 1e6,
+                           "density_ms": m2[0], "density_gbs": BYTES_DENSITY[1] * sites / (m2[0] * 1e-3) / 1e9,
+                           "collide_ms": m2[1], "collide_gbs": BYTES_COLLIDE[1] * sites / (m2[1] * 1e-3) / 1e9,
+                           "collide_frac": BYTES_COLLIDE[1] * sites / (m2[1] * 1e-3) / 1e9 / peak}
+
         # autotuned execution configuration (mode, tile height) and its sustained rate
         tuned_ms = b.autotune(64, None)
-        mode, tyh = b.config()
+        tmode, tyh = b.config()
         b.synchronize()
         ev0.record(stream)
         b.step(256)
         ev1.record(stream)
         ev1.synchronize()
-        out["autotuned"] = {"mode": ["launch", "persistent"][mode], "tile_height": tyh,
+        out["autotuned"] = {"mode": ["launch", "persistent", "fused"][tmode], "tile_height": tyh,
                             "trial_ms_per_step": tuned_ms,
                             "sustained_mlups": sites * 256 / (ev0.elapsed_time(ev1) * 1e-3) / 1e6}
 
         # Laplace fit at ratio 1 after the run so far (not converged; sanity only)
         # FP64 on the same batch
         b64 = make_batch(lb, specs, fields, lb.LB_FP64, sptr)
+        b64.set_config(mode, 4)
         b64.profile(3, flush.data_ptr(), FLUSH_BYTES)
         k64 = max(10, args.steps // 4)
         ms64 = b64.profile(k64, flush.data_ptr(), FLUSH_BYTES)
         out["fp64_same_workload"] = {
             "mlups": sites / (ms64[2] * 1e-3) / 1e6, "ms_per_step": ms64[2], "steps": k64,
-            "collide_ms": ms64[1], "density_ms": ms64[0],
-            "collide_achieved_gbs": BYTES_COLLIDE[0] * sites / (ms64[1] * 1e-3) / 1e9,
+            "kernel_ms": ms64[1], "density_ms": ms64[0],
+            "kernel_achieved_gbs": kbytes[0] * sites / (ms64[1] * 1e-3) / 1e9,
         }
         out["fp32_over_fp64"] = value / out["fp64_same_workload"]["mlups"]
         del b64
@@ -393,14 +410,19 @@ def main():
         for prec, name in ((lb.LB_FP32, "fp32"), (lb.LB_FP64, "fp64")):
             L = lb.Lattice(4096, 4096, tau=(3.0, 1.0), precision=prec, stream=sptr, **C6)
             L.set_fields(rho4k)
-            L.profile(3)
-            k = 20 if prec == lb.LB_FP32 else 8
-            m = L.profile(k)
             n4 = 4096 * 4096
+            k = 20 if prec == lb.LB_FP32 else 8
+            L.set_config(lb.LB_MODE_FUSED, 4)
+            L.profile(3)
+            m = L.profile(k)
+            L.set_config(lb.LB_MODE_LAUNCH, 4)
+            L.profile(2)
+            m2 = L.profile(k)
             big[name] = {"mlups": n4 / (m[2] * 1e-3) / 1e6, "ms_per_step": m[2], "steps": k,
-                         "collide_ms": m[1], "density_ms": m[0],
-                         "collide_achieved_gbs": BYTES_COLLIDE[prec] * n4 / (m[1] * 1e-3) / 1e9,
-                         "collide_frac_of_measured_hbm": BYTES_COLLIDE[prec] * n4 / (m[1] * 1e-3) / 1e9 / peak,
+                         "fused_achieved_gbs": BYTES_FUSED[prec] * n4 / (m[1] * 1e-3) / 1e9,
+                         "fused_frac_of_measured_hbm": BYTES_FUSED[prec] * n4 / (m[1] * 1e-3) / 1e9 / peak,
+                         "two_pass_mlups": n4 / (m2[2] * 1e-3) / 1e6, "collide_ms": m2[1], "density_ms": m2[0],
+                         "collide_frac_of_measured_hbm": BYTES_COLLIDE[prec] * n4 / (m2[1] * 1e-3) / 1e9 / peak,
                          "step_effective_gbs_floor": (144 if prec else 288) * n4 / (m[2] * 1e-3) / 1e9}
             del L
         out["large_dense_4096"] = big

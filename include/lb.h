@@ -65,9 +65,14 @@ extern "C" {
  *   blocks take (step, phase, tile) work items from an atomic queue and wait,
  *   with a bounded spin, only for the tiles of their own lattice that an item
  *   depends on; replayed as a CUDA graph.  A wait that runs out (default 2 s)
- *   ends the launch and the next synchronising call returns LB_ETIMEOUT. */
+ *   ends the launch and the next synchronising call returns LB_ETIMEOUT.
+ * LB_MODE_FUSED: each time step is one launch: every block forms the
+ *   densities of its tile and 2-node halo from the populations itself (no
+ *   separate density pass), then runs the fused force / collision / push;
+ *   replayed 32 steps per CUDA graph. */
 #define LB_MODE_LAUNCH 0
 #define LB_MODE_PERSISTENT 1
+#define LB_MODE_FUSED 2
 
 /* Densities the interaction stencils see beyond a wall (ghost rows
  * y = -1, -2 and y = ny, ny + 1). */
@@ -161,7 +166,8 @@ int lb_step(lb_handle *h, int64_t n);
  * (once) if a bounded device-side wait of a persistent launch expired. */
 int lb_synchronize(lb_handle *h);
 
-/* Execution configuration: mode (LB_MODE_LAUNCH or LB_MODE_PERSISTENT) and
+/* Execution configuration: mode (LB_MODE_LAUNCH, LB_MODE_PERSISTENT or
+ * LB_MODE_FUSED) and
  * tile height (2, 4 or 8 nodes; tiles are 32 nodes wide, one thread per
  * node).  Default: LB_MODE_LAUNCH, 4.  Results do not depend on it. */
 int lb_set_config(lb_handle *h, int32_t mode, int32_t tile_height);
@@ -215,8 +221,10 @@ int lb_load(lb_handle *h, const void *buf, size_t len);
 
 /* Time nsteps time steps kernel by kernel with CUDA events on the handle's
  * stream (direct launches, no graph):
- *   ms[0]  mean duration of one density-pass launch
- *   ms[1]  mean duration of one fused force/collide/stream launch
+ *   ms[0]  mean duration of one density-pass launch (0 in LB_MODE_FUSED)
+ *   ms[1]  mean duration of one fused force/collide/stream launch (in
+ *          LB_MODE_FUSED the one-pass kernel; LB_MODE_PERSISTENT is timed as
+ *          LB_MODE_LAUNCH)
  *   ms[2]  mean duration of one whole time step (both launches)
  * If flush_bytes > 0, the caller's device buffer flush_buf of that size is
  * overwritten before every step, outside the timed intervals, so that each

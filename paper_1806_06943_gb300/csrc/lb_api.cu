@@ -193,17 +193,20 @@ struct lb_engine {
             return lbk::Launch<double>::density((const lbk::Lat<double> *)d_lats, d_tiles, off, cnt, par, 4, stream);
         return lbk::Launch<float>::density((const lbk::Lat<float> *)d_lats, d_tiles, off, cnt, par, 4, stream);
     }
-    // one time step as two launches over the time-step tiles of height ty
+    // one time step over the time-step tiles of height ty: two launches, or
+    // one in the fused mode
     cudaError_t launch_step(int par)
     {
         const int ti = ty_index(ty), nt = (int)stiles[ti].size();
         cudaError_t e;
         if (precision == LB_FP64) {
             const lbk::Lat<double> *L = (const lbk::Lat<double> *)d_lats;
+            if (mode == LB_MODE_FUSED) return lbk::Launch<double>::fused(L, d_stiles[ti], 0, nt, par, ty, stream);
             e = lbk::Launch<double>::density(L, d_stiles[ti], 0, nt, par, ty, stream);
             if (e == cudaSuccess) e = lbk::Launch<double>::collide(L, d_stiles[ti], 0, nt, par, ty, stream);
         } else {
             const lbk::Lat<float> *L = (const lbk::Lat<float> *)d_lats;
+            if (mode == LB_MODE_FUSED) return lbk::Launch<float>::fused(L, d_stiles[ti], 0, nt, par, ty, stream);
             e = lbk::Launch<float>::density(L, d_stiles[ti], 0, nt, par, ty, stream);
             if (e == cudaSuccess) e = lbk::Launch<float>::collide(L, d_stiles[ti], 0, nt, par, ty, stream);
         }
@@ -333,7 +336,8 @@ struct lb_engine {
 
     int set_config(int m, int tyv)
     {
-        if (m != LB_MODE_LAUNCH && m != LB_MODE_PERSISTENT) return fail(LB_EINVAL, "mode must be LB_MODE_LAUNCH or LB_MODE_PERSISTENT");
+        if (m != LB_MODE_LAUNCH && m != LB_MODE_PERSISTENT && m != LB_MODE_FUSED)
+            return fail(LB_EINVAL, "mode must be LB_MODE_LAUNCH, LB_MODE_PERSISTENT or LB_MODE_FUSED");
         if (ty_index(tyv) < 0) return fail(LB_EINVAL, "tile height must be 2, 4 or 8");
         if (m != mode || tyv != ty) drop_graph();
         mode = m;
@@ -362,16 +366,21 @@ struct lb_engine {
         for (int s = 0; s < nsteps && ce == cudaSuccess; ++s) {
             if (flush_bytes) ce = cudaMemsetAsync(flush, s & 0xff, flush_bytes, stream);
             if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s], stream);
+            const bool one = mode == LB_MODE_FUSED;
             if (precision == LB_FP64) {
                 const lbk::Lat<double> *L = (const lbk::Lat<double> *)d_lats;
-                if (ce == cudaSuccess) ce = lbk::Launch<double>::density(L, d_stiles[ti], 0, nt, parity, ty, stream);
+                if (ce == cudaSuccess && !one) ce = lbk::Launch<double>::density(L, d_stiles[ti], 0, nt, parity, ty, stream);
                 if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s + 1], stream);
-                if (ce == cudaSuccess) ce = lbk::Launch<double>::collide(L, d_stiles[ti], 0, nt, parity, ty, stream);
+                if (ce == cudaSuccess)
+                    ce = one ? lbk::Launch<double>::fused(L, d_stiles[ti], 0, nt, parity, ty, stream)
+                             : lbk::Launch<double>::collide(L, d_stiles[ti], 0, nt, parity, ty, stream);
             } else {
                 const lbk::Lat<float> *L = (const lbk::Lat<float> *)d_lats;
-                if (ce == cudaSuccess) ce = lbk::Launch<float>::density(L, d_stiles[ti], 0, nt, parity, ty, stream);
+                if (ce == cudaSuccess && !one) ce = lbk::Launch<float>::density(L, d_stiles[ti], 0, nt, parity, ty, stream);
                 if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s + 1], stream);
-                if (ce == cudaSuccess) ce = lbk::Launch<float>::collide(L, d_stiles[ti], 0, nt, parity, ty, stream);
+                if (ce == cudaSuccess)
+                    ce = one ? lbk::Launch<float>::fused(L, d_stiles[ti], 0, nt, parity, ty, stream)
+                             : lbk::Launch<float>::collide(L, d_stiles[ti], 0, nt, parity, ty, stream);
             }
             if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s + 2], stream);
             if (ce == cudaSuccess) {
@@ -460,7 +469,7 @@ struct lb_engine {
         double best = std::numeric_limits<double>::infinity();
         int bm = mode, bty = ty;
         cudaError_t ce = cudaMemcpyAsync(snap, d_pool, pool_bytes, cudaMemcpyDeviceToDevice, stream);
-        for (int m = LB_MODE_LAUNCH; m <= LB_MODE_PERSISTENT && ce == cudaSuccess && rc == LB_OK; ++m)
+        for (int m = LB_MODE_LAUNCH; m <= LB_MODE_FUSED && ce == cudaSuccess && rc == LB_OK; ++m)
             for (int tyv : kTileHeights) {
                 if ((rc = set_config(m, tyv))) break;
                 if ((rc = step(chunk_steps()))) break;            // warm-up, builds the graph

@@ -539,6 +539,109 @@ __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restric
     collide_push_dir<real, 8, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
 }
 
+// ---- one-pass step ------------------------------------------------------------
+
+// Density of node (gx, gy) straight from its populations (FP32: plus its
+// reference density): the same sum, in the same order, as the density pass.
+template <typename real, bool kCG>
+__device__ __forceinline__ real node_density(const Lat<real> &L, int k, int gx, int gy, int parity)
+{
+    const size_t c = (size_t)gy * L.pitch + gx;
+    const real *__restrict__ f = L.f[parity];
+    real v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = ldg_state<kCG>(&f[(size_t)(k * 9 + i) * L.plane + c]);
+    real r = zeroth_moment<real>(v);
+    if constexpr (kOffset<real>) r = ldg_state<kCG>(&L.rho[parity][(size_t)k * L.plane + c]) + r;
+    return r;
+}
+
+// One time step of one tile in a single pass: each thread forms its node's
+// densities from the populations it loads anyway; the 2-node halo (and the
+// slots of a ragged tile's missing nodes) is formed from the neighbours'
+// populations, mostly L2 hits.  FP32 writes the node's density as the next
+// step's reference.  Then the fused force + collision + push of collide_site.
+template <typename real, int TYv, bool kCG>
+__device__ __forceinline__ void fused_tile(const Lat<real> *__restrict__ lats, int4 t, int parity,
+                                           CollideSmem<real, TYv> &sm)
+{
+    constexpr int SHv = TYv + 2 * HALO;
+    const Lat<real> &G = lats[t.x];
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    if (tid < (int)(sizeof(Lat<real>) / 4))
+        reinterpret_cast<uint32_t *>(&sm.L)[tid] = reinterpret_cast<const uint32_t *>(&G)[tid];
+    const int nx = G.nx, ny = G.ny;
+    const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
+    const bool valid = x < nx && y < ny;
+    const real *__restrict__ fc = G.f[parity];
+    real *__restrict__ fn = G.f[parity ^ 1];
+    const size_t c = valid ? (size_t)y * G.pitch + x : 0;
+    real fk[2][9];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fk[k][i] = valid ? ldg_state<kCG>(&fc[(size_t)(k * 9 + i) * G.plane + c]) : (real)0;
+    const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
+    if (valid) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            real r = zeroth_moment<real>(fk[k]);
+            if constexpr (kOffset<real>) {
+                r = ldg_state<kCG>(&G.rho[parity][(size_t)k * G.plane + c]) + r;
+                G.rho[parity ^ 1][(size_t)k * G.plane + c] = r;
+            }
+            sm.srho[k][cy][cx] = r;
+            sm.spsi[k][cy][cx] = psi_of<real>(r);
+        }
+    }
+    // halo, and the slots of nodes a ragged tile does not own
+    for (int idx = tid; idx < SW * SHv; idx += TX * TYv) {
+        const int sx = idx % SW, sy = idx / SW;
+        const int gxr = t.y + sx - HALO, gyr = t.z + sy - HALO;
+        const bool own = sx >= HALO && sx < HALO + TX && sy >= HALO && sy < HALO + TYv && gxr < nx && gyr < ny;
+        if (own) continue;
+        const int gx = wrap_index(gxr, nx);
+        int gy = gyr;
+        real rA, rB;
+        bool fixed = false;
+        if (gy < 0 || gy >= ny) {
+            if (G.walls) {
+                if (G.wall_mode == 1) {
+                    rA = G.wall_rho[0];
+                    rB = G.wall_rho[1];
+                    fixed = true;
+                } else {
+                    gy = gy < 0 ? -1 - gy : 2 * ny - 1 - gy;
+                    gy = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);  // rows no valid node reads
+                }
+            } else {
+                gy = wrap_index(gy, ny);
+            }
+        }
+        if (!fixed) {
+            rA = node_density<real, kCG>(G, 0, gx, gy, parity);
+            rB = node_density<real, kCG>(G, 1, gx, gy, parity);
+        }
+        sm.srho[0][sy][sx] = rA;
+        sm.srho[1][sy][sx] = rB;
+        sm.spsi[0][sy][sx] = psi_of<real>(rA);
+        sm.spsi[1][sy][sx] = psi_of<real>(rB);
+    }
+    __syncthreads();
+    if (!valid) return;
+    const bool inner = t.y >= 1 && t.y + TX + 1 <= sm.L.nx && t.z >= 1 && t.z + TYv + 1 <= sm.L.ny;
+    if (inner) collide_site<real, true, SHv>(sm.L, fn, sm.srho, sm.spsi, fk, x, y, cx, cy);
+    else collide_site<real, false, SHv>(sm.L, fn, sm.srho, sm.spsi, fk, x, y, cx, cy);
+}
+
+template <typename real, int TYv>
+__global__ void __launch_bounds__(TX *TYv, kCollideMinBlocks<real, TYv>)
+    k_fused(const Lat<real> *__restrict__ lats, const int4 *__restrict__ tiles, int tile_offset, int parity)
+{
+    __shared__ CollideSmem<real, TYv> sm;
+    fused_tile<real, TYv, false>(lats, tiles[tile_offset + blockIdx.x], parity, sm);
+}
+
 // ---- persistent launch over many time steps -----------------------------------
 
 // Bounded wait until *ctr >= need.  Gives up when another block has flagged an

@@ -16,6 +16,9 @@ struct Launch {
                                int ty, cudaStream_t s);
     static cudaError_t collide(const Lat<real> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
                                int ty, cudaStream_t s);
+    // one time step in one pass (densities formed in the kernel)
+    static cudaError_t fused(const Lat<real> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
+                             int ty, cudaStream_t s);
     // nsteps time steps of all tiles in one persistent launch of `blocks`
     // blocks (ctl, dens_done, coll_done cleared by the caller beforehand)
     static cudaError_t persistent(const Lat<real> *lats, const int4 *tiles, const int *lat_ntiles, int n_tiles,

@@ -36,6 +36,20 @@ cudaError_t Launch<real>::collide(const Lat<real> *lats, const int4 *tiles, int 
 }
 
 template <typename real>
+cudaError_t Launch<real>::fused(const Lat<real> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
+                                int ty, cudaStream_t s)
+{
+    if (n_tiles <= 0) return cudaSuccess;
+    switch (ty) {
+    case 2: k_fused<real, 2><<<n_tiles, dim3(TX, 2), 0, s>>>(lats, tiles, tile_offset, parity); break;
+    case 4: k_fused<real, 4><<<n_tiles, dim3(TX, 4), 0, s>>>(lats, tiles, tile_offset, parity); break;
+    case 8: k_fused<real, 8><<<n_tiles, dim3(TX, 8), 0, s>>>(lats, tiles, tile_offset, parity); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t Launch<real>::persistent(const Lat<real> *lats, const int4 *tiles, const int *lat_ntiles, int n_tiles,
                                      int nsteps, int parity0,
                                      void *ctl, unsigned *dens_done, unsigned *coll_done, int *err,
