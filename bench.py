@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--mode", default="fused", choices=["fused", "launch"],
                     help="time step as one pass (fused) or density pass + fused kernel (launch)")
+    ap.add_argument("--tile-height", type=int, default=8, choices=[2, 4, 8])
     return ap.parse_args()
 
 
@@ -300,9 +301,10 @@ def main():
     prec = lb.LB_FP32 if args.precision == "fp32" else lb.LB_FP64
     b = make_batch(lb, specs, fields, prec, sptr)
     mode = lb.LB_MODE_FUSED if args.mode == "fused" else lb.LB_MODE_LAUNCH
-    b.set_config(mode, 4)
+    b.set_config(mode, args.tile_height)
     kbytes = BYTES_FUSED if mode == lb.LB_MODE_FUSED else BYTES_COLLIDE
-    kname = ("k_fused" if mode == lb.LB_MODE_FUSED else "k_collide") + f"<{'float' if prec else 'double'}, 4>"
+    kname = (("k_fused" if mode == lb.LB_MODE_FUSED else "k_collide")
+             + f"<{'float' if prec else 'double'}, {args.tile_height}>")
 
     # warm-up (untimed), then the timed region: K steps, barrier + sync on both sides
     b.profile(args.warmup, flush.data_ptr(), FLUSH_BYTES)

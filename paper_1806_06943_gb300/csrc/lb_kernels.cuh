@@ -594,14 +594,10 @@ __device__ __forceinline__ void fused_tile(const Lat<real> *__restrict__ lats, i
             sm.spsi[k][cy][cx] = psi_of<real>(r);
         }
     }
-    // halo, and the slots of nodes a ragged tile does not own
-    for (int idx = tid; idx < SW * SHv; idx += TX * TYv) {
-        const int sx = idx % SW, sy = idx / SW;
-        const int gxr = t.y + sx - HALO, gyr = t.z + sy - HALO;
-        const bool own = sx >= HALO && sx < HALO + TX && sy >= HALO && sy < HALO + TYv && gxr < nx && gyr < ny;
-        if (own) continue;
-        const int gx = wrap_index(gxr, nx);
-        int gy = gyr;
+    // densities of one staged slot from the populations of its node
+    auto stage_slot = [&](int sx, int sy) {
+        const int gx = wrap_index(t.y + sx - HALO, nx);
+        int gy = t.z + sy - HALO;
         real rA, rB;
         bool fixed = false;
         if (gy < 0 || gy >= ny) {
@@ -626,6 +622,31 @@ __device__ __forceinline__ void fused_tile(const Lat<real> *__restrict__ lats, i
         sm.srho[1][sy][sx] = rB;
         sm.spsi[0][sy][sx] = psi_of<real>(rA);
         sm.spsi[1][sy][sx] = psi_of<real>(rB);
+    };
+    // the halo ring, enumerated compactly: two rows above, two below, then
+    // the two columns on each side of the tile's rows
+    constexpr int kRing = 4 * SW + 4 * TYv;
+    for (int h = tid; h < kRing; h += TX * TYv) {
+        int sx, sy;
+        if (h < 2 * SW) {
+            sy = h / SW;
+            sx = h % SW;
+        } else if (h < 4 * SW) {
+            sy = TYv + HALO + (h - 2 * SW) / SW;
+            sx = (h - 2 * SW) % SW;
+        } else {
+            const int q = h - 4 * SW;
+            sy = HALO + q / 4;
+            sx = (q % 4 < 2) ? q % 4 : TX + q % 4;
+        }
+        stage_slot(sx, sy);
+    }
+    // a ragged tile's slots without a node of their own hold wrapped copies
+    if (t.y + TX > nx || t.z + TYv > ny) {
+        for (int q = tid; q < TX * TYv; q += TX * TYv) {
+            const int sx = HALO + q % TX, sy = HALO + q / TX;
+            if (t.y + sx - HALO >= nx || t.z + sy - HALO >= ny) stage_slot(sx, sy);
+        }
     }
     __syncthreads();
     if (!valid) return;
