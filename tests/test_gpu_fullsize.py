@@ -1,0 +1,110 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the
+benchmark times (one-pass step, tiles of 32 x 8, FP32 and FP64): sampled
+nodes against the oracle, which advances a 21 x 21 patch of the initial field
+around each sampled node.  After two steps a node depends only on nodes
+within 6 lattice units, and its diagnostics (forces included) on nodes within
+8, so the patch centre sees exactly the full lattice's values.  Plus mass
+conservation over 100 steps at full size."""
+import numpy as np
+import pytest
+
+from paper_1806_06943_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+C6 = dict(G_AB=3.0, G1=-7.4, G2=6.4)
+HW = 10   # patch half-width
+
+
+@pytest.fixture(scope="module")
+def emulsion4096():
+    rho0, _, _, _ = W.random_emulsion(4096, 4096, 0.6, 8.0, 20.0, seed=W.BASE_SEED + 4)
+    return rho0
+
+
+@pytest.fixture(scope="module")
+def lbmod():
+    from paper_1806_06943_gb300 import build
+    build.build()
+    from paper_1806_06943_gb300 import lb
+    return lb
+
+
+def patch(field, cx, cy):
+    ny, nx = field.shape[-2:]
+    ys = np.arange(cy - HW, cy + HW + 1) % ny
+    xs = np.arange(cx - HW, cx + HW + 1) % nx
+    return np.ascontiguousarray(field[..., ys[:, None], xs[None, :]])
+
+
+def check_samples(oracle_mod, rho0, tau, fields, samples, tol_rho, tol_u):
+    """Errors are normwise: relative to the lattice's largest value of the
+    field (c12 reading), as in the other parity tests."""
+    scales = {k: np.max(np.abs(fields[k])) for k in ("rho", "ubar", "mom")}
+    for (cx, cy) in samples:
+        o = oracle_mod.OracleSim(2 * HW + 1, 2 * HW + 1, tau=tau, **C6)
+        o.set_fields(patch(rho0, cx, cy))
+        o.step(2)
+        fo = o.fields()
+        for key, tol in (("rho", tol_rho), ("ubar", tol_u), ("mom", tol_u)):
+            ref = fo[key][..., HW, HW]
+            got = fields[key][..., cy, cx]
+            assert np.max(np.abs(got - ref)) <= tol * scales[key], (key, cx, cy, got, ref)
+
+
+def sample_nodes(rng, nx, ny, n=12):
+    return [(int(rng.integers(0, nx)), int(rng.integers(0, ny))) for _ in range(n)]
+
+
+@pytest.mark.parametrize("precision,tol_rho,tol_u", [(0, 1e-13, 1e-12), (1, 1e-6, 1e-5)])
+def test_dense_emulsion_4096_sampled(lbmod, oracle_mod, emulsion4096, precision, tol_rho, tol_u):
+    n = 4096
+    rho0 = emulsion4096
+    tau = (3.0, 1.0)
+    L = lbmod.Lattice(n, n, tau=tau, precision=precision, **C6)
+    L.set_config(lbmod.LB_MODE_FUSED, 8)
+    L.set_fields(rho0)
+    L.step(2)
+    f = L.fields()
+    rng = np.random.default_rng(7)
+    # half of the samples on droplet interfaces, where the stencils matter
+    edge = np.argwhere(np.abs(rho0[0] - np.roll(rho0[0], -1, axis=1)) > 0.5)
+    picks = [tuple(int(v) for v in edge[i][::-1]) for i in rng.choice(len(edge), 6, replace=False)]
+    check_samples(oracle_mod, rho0, tau, f, picks + sample_nodes(rng, n, n, 6), tol_rho, tol_u)
+
+
+@pytest.mark.parametrize("precision,tol_rho,tol_u", [(0, 1e-13, 1e-12), (1, 1e-6, 1e-5)])
+def test_laplace_sweep_24_sampled(lbmod, oracle_mod, precision, tol_rho, tol_u):
+    specs = W.laplace_sweep_specs()
+    fields0 = [W.droplet(s["nx"], s["ny"], s["R"], seed=W.BASE_SEED + 1 + i) for i, s in enumerate(specs)]
+    b = lbmod.Batch([dict(nx=s["nx"], ny=s["ny"], tau=s["tau"]) for s in specs], precision=precision, **C6)
+    b.set_config(lbmod.LB_MODE_FUSED, 8)
+    for i, r in enumerate(fields0):
+        b.set_fields(i, r)
+    b.step(2)
+    rng = np.random.default_rng(11)
+    for i in (0, 7, 13, 23):
+        s = specs[i]
+        f = b.fields(i)
+        cx, cy = s["nx"] // 2, s["ny"] // 2
+        ring = [(int(cx + s["R"] * np.cos(a)), int(cy + s["R"] * np.sin(a))) for a in rng.uniform(0, 2 * np.pi, 3)]
+        check_samples(oracle_mod, fields0[i], s["tau"], f, ring + sample_nodes(rng, s["nx"], s["ny"], 2),
+                      tol_rho, tol_u)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-6)])
+def test_mass_conserved_at_full_size(lbmod, emulsion4096, precision, tol):
+    n = 4096
+    rho0 = emulsion4096
+    L = lbmod.Lattice(n, n, tau=(3.0, 1.0), precision=precision, **C6)
+    L.set_config(lbmod.LB_MODE_FUSED, 8)
+    L.set_fields(rho0)
+    o0 = L.observables()
+    L.step(100)
+    o1 = L.observables()
+    for k in ("massA", "massB"):
+        assert abs(o1[k] - o0[k]) <= tol * o0[k], (k, o0[k], o1[k])
+    M = o0["massA"] + o0["massB"]
+    for a in ("x", "y"):
+        p0, p1 = o0["momA" + a] + o0["momB" + a], o1["momA" + a] + o1["momB" + a]
+        assert abs(p1 - p0) <= 10 * tol * M
