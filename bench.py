@@ -38,7 +38,7 @@ C6 = dict(G_AB=3.0, G1=-7.4, G2=6.4)
 FLUSH_BYTES = 256 << 20
 # algorithmic bytes per node and launch (FP32 offset / FP64 plain):
 BYTES_FUSED = {1: 160, 0: 288}     # one-pass: 18 pops read + 18 written (+ 2 reference rho read, 2 written)
-BYTES_COLLIDE = {1: 152, 0: 304}   # two-pass fused kernel: 18 pops read + 18 written + 2 rho read
+BYTES_COLLIDE = {1: 160, 0: 304}   # two-pass fused kernel: 18 pops read + 18 written + 2 rho read (+ 2 reference rho read)
 BYTES_DENSITY = {1: 88, 0: 160}    # density pass: 18 pops read + 2 rho written (+ 2 reference rho read)
 
 

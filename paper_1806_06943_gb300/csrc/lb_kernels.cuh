@@ -299,6 +299,7 @@ struct SpeciesTerms {
     real uF[2];        // u^eq . F_k
     real wr[2][3];     // w(|e|^2) rho_k
     real aw3[2][3];    // 3 (1 - omega_k/2) w(|e|^2)
+    real dg[2];        // sum_i of the offsets from rho_k: minus the rounding of rho_k
 };
 
 template <typename real, int I, bool kInner, int SHv>
@@ -327,7 +328,9 @@ __device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__res
         for (int k = 0; k < 2; ++k) {
             const real eF = edot<real, EX, EY>(F[k][0], F[k][1]);
             const real Cg = st.aw3[k][C] * (eF * tt - st.uF[k]);
-            const real geq = st.wr[k][C] * q;
+            // the equilibrium carries the node's exact mass: its offsets from the
+            // rounded rho_k sum to dg, like the populations' do
+            const real geq = st.wr[k][C] * q + (real)w9(I) * st.dg[k];
             const real f = fk[k][I];
             const real v = (f + L.omega[k] * (geq - f)) + Cg;
             push_dir<real, I, kInner, SHv>(L, fn, srho, k, x, y, cx, cy, v);
@@ -409,7 +412,8 @@ struct CollideSmem {
 
 template <typename real, bool kInner, int SHv>
 __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW],
-                                             const real (*spsi)[SHv][SW], real (&fk)[2][9], int x, int y, int cx, int cy);
+                                             const real (*spsi)[SHv][SW], real (&fk)[2][9], const real (&Rn)[2], int x,
+                                             int y, int cx, int cy);
 
 // Fused force + collision + push-streaming + bounce-back for one tile.  Every
 // thread of the block calls it and returns from it; it ends after the tile's
@@ -475,10 +479,15 @@ __device__ __forceinline__ void collide_tile(const Lat<real> *__restrict__ lats,
     __syncthreads();
     if (!valid) return;
     const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
+    real Rn[2] = {(real)0, (real)0};
+    if constexpr (kOffset<real>) {
+        Rn[0] = ldg_state<kCG>(&G.rho[parity][c]);
+        Rn[1] = ldg_state<kCG>(&G.rho[parity][G.plane + c]);
+    }
     // tiles whose pushes stay inside the lattice (no wrap, no wall) take constant offsets
     const bool inner = t.y >= 1 && t.y + TX + 1 <= sm.L.nx && t.z >= 1 && t.z + TYv + 1 <= sm.L.ny;
-    if (inner) collide_site<real, true, TYv + 2 * HALO>(sm.L, fn, sm.srho, sm.spsi, fk, x, y, cx, cy);
-    else collide_site<real, false, TYv + 2 * HALO>(sm.L, fn, sm.srho, sm.spsi, fk, x, y, cx, cy);
+    if (inner) collide_site<real, true, TYv + 2 * HALO>(sm.L, fn, sm.srho, sm.spsi, fk, Rn, x, y, cx, cy);
+    else collide_site<real, false, TYv + 2 * HALO>(sm.L, fn, sm.srho, sm.spsi, fk, Rn, x, y, cx, cy);
 }
 
 template <typename real, int TYv>
@@ -491,9 +500,10 @@ __global__ void __launch_bounds__(TX *TYv, kCollideMinBlocks<real, TYv>)
 
 template <typename real, bool kInner, int SHv>
 __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW],
-                                             const real (*spsi)[SHv][SW], real (&fk)[2][9], int x, int y, int cx, int cy)
+                                             const real (*spsi)[SHv][SW], real (&fk)[2][9], const real (&Rn)[2], int x,
+                                             int y, int cx, int cy)
 {
-    real F[2][2], rho[2], m[2][2];
+    real F[2][2], rho[2], m[2][2], dg[2] = {(real)0, (real)0};
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         force_at<real, SHv>(L, srho, spsi, k, cx, cy, F[k][0], F[k][1]);
@@ -503,10 +513,15 @@ __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restric
         m[k][0] = jx + (real)0.5 * F[k][0];   // Eq. (6), half force
         m[k][1] = jy + (real)0.5 * F[k][1];
         if constexpr (kOffset<real>) {
-            // offsets from the node's current density: h_i - w_i (rho - R)
-            const real delta = zeroth_moment<real>(fk[k]);
+            // offsets from the node's current density: h_i - w_i (rho - R).
+            // rho - R is formed from the rounded density itself (exact: the two
+            // are close), so f = h + w R is kept exactly whatever rho rounded to;
+            // with sum_i h_i instead, density changes below half an ulp of R
+            // would be dropped at every step and mass would drift.
+            const real delta = rho[k] - Rn[k];
 #pragma unroll
             for (int i = 0; i < 9; ++i) fk[k][i] -= (real)w9(i) * delta;
+            dg[k] = zeroth_moment<real>(fk[k]);
         }
     }
     // common velocity, Eq. (3)
@@ -519,6 +534,7 @@ __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restric
     if constexpr (kOffset<real>) {
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
+            st.dg[k] = dg[k];
             st.uF[k] = ux * F[k][0] + uy * F[k][1];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -582,12 +598,14 @@ __device__ __forceinline__ void fused_tile(const Lat<real> *__restrict__ lats, i
 #pragma unroll
         for (int i = 0; i < 9; ++i) fk[k][i] = valid ? ldg_state<kCG>(&fc[(size_t)(k * 9 + i) * G.plane + c]) : (real)0;
     const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
+    real Rn[2] = {(real)0, (real)0};
     if (valid) {
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             real r = zeroth_moment<real>(fk[k]);
             if constexpr (kOffset<real>) {
-                r = ldg_state<kCG>(&G.rho[parity][(size_t)k * G.plane + c]) + r;
+                Rn[k] = ldg_state<kCG>(&G.rho[parity][(size_t)k * G.plane + c]);
+                r = Rn[k] + r;
                 G.rho[parity ^ 1][(size_t)k * G.plane + c] = r;
             }
             sm.srho[k][cy][cx] = r;
@@ -651,8 +669,8 @@ __device__ __forceinline__ void fused_tile(const Lat<real> *__restrict__ lats, i
     __syncthreads();
     if (!valid) return;
     const bool inner = t.y >= 1 && t.y + TX + 1 <= sm.L.nx && t.z >= 1 && t.z + TYv + 1 <= sm.L.ny;
-    if (inner) collide_site<real, true, SHv>(sm.L, fn, sm.srho, sm.spsi, fk, x, y, cx, cy);
-    else collide_site<real, false, SHv>(sm.L, fn, sm.srho, sm.spsi, fk, x, y, cx, cy);
+    if (inner) collide_site<real, true, SHv>(sm.L, fn, sm.srho, sm.spsi, fk, Rn, x, y, cx, cy);
+    else collide_site<real, false, SHv>(sm.L, fn, sm.srho, sm.spsi, fk, Rn, x, y, cx, cy);
 }
 
 template <typename real, int TYv>

@@ -5,18 +5,21 @@ Tolerances (normwise relative error, ||x_gpu - x_ref||_inf / ||x_ref||_inf,
 per field, because velocities are near zero at many nodes):
   FP64 populations, densities and velocities ........ 1e-12
   FP32 densities .................................... 1e-5
-  FP32 velocities ................................... 1e-4 (see below)
+  FP32 velocities ................................... 1e-5
   FP32 Laplace pressure jump and effective viscosity  1e-3 relative
 FP64 reductions (mass, momentum, flux) are compared at 1e-12 relative to
 their scale; derived observables at 1e-10.
 
-FP32 velocity bound: at an interface node the momentum balance is a
+FP32 velocity error: at an interface node the momentum balance is a
 difference of a pressure-gradient flux cs^2 |grad rho| ~ 0.03 and the forces;
 single-precision densities (half ulp ~ 3e-8 near rho = 1) make that balance
 err by ~1e-8 per step, a random forcing whose effect accumulates over the
 viscous relaxation time of the drop (R^2/nu ~ 900 steps): sqrt(900) * 1e-8 ~
-3e-7, i.e. 3e-5 of the 0.0095 spurious-current maximum.  Runs that differ only
-in the order of rounding land between 2e-5 and 5e-5, so the bound is 1e-4."""
+3e-7, i.e. 3e-5 of the 0.0095 spurious-current maximum at worst.  With the
+node's density split exactly into reference and offsets (no mass drift) the
+C1 droplet lands just under 1e-5.  Where droplets advect (the channel) an
+interface displaced by a velocity error moves densities too, and both fields
+are held to 1e-4."""
 import numpy as np
 import pytest
 
@@ -117,7 +120,7 @@ def test_fp32_offset_c1_droplet(oracle_mod, lbmod):
     fo, fg = o.fields(), g.fields()
     er, eu = nrel(fg["rho"], fo["rho"]), nrel(fg["ubar"], fo["ubar"])
     assert er <= 1e-5, er
-    assert eu <= 1e-4, eu
+    assert eu <= 1e-5, eu
     oo = o.observables((32, 32, 12))
     g.set_probe(32, 32, 12)
     og = g.observables()
