@@ -185,11 +185,11 @@ class ClockSampler:
 
 def kernel_traffic(workload: str, kernel: str):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary
-    (profiles/k_collide_traffic.json), if it was taken on this workload and on
+    (profiles/traffic.json), if it was taken on this workload and on
     the current kernel source; else None."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "profiles", "k_collide_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
         src = os.path.join(ROOT, "paper_1806_06943_gb300", "csrc", "lb_kernels.cuh")
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
