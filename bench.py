@@ -53,7 +53,7 @@ def parse():
                     choices=["laplace_sweep_24", "dense_emulsion_4096", "dense_emulsion_2048"],
                     help="main-leg workload (the dense emulsions are single periodic lattices)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--mode", default="fused", choices=["fused", "launch"],
+    ap.add_argument("--mode", default="tma", choices=["tma", "fused", "launch"],
                     help="time step as one pass (fused) or density pass + fused kernel (launch)")
     ap.add_argument("--tile-height", type=int, default=8, choices=[2, 4, 8])
     return ap.parse_args()
@@ -183,18 +183,30 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_traffic(workload: str, kernel: str):
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary
-    (profiles/traffic.json), if it was taken on this workload and on
-    the current kernel source; else None."""
+KERNEL_SOURCES = ("lb_kernels.cuh", "lb_tma.cu")
+
+
+def kernel_source_sha1() -> str:
+    """SHA-1 over the kernel sources (lb_kernels.cuh, then lb_tma.cu)."""
     import hashlib
+    h = hashlib.sha1()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1806_06943_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def kernel_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch of a step kernel from the committed ncu summary
+    (profiles/traffic.json: a list of entries), if one was taken on this
+    workload, on this kernel and on the current kernel sources; else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            d = json.load(f)
-        src = os.path.join(ROOT, "paper_1806_06943_gb300", "csrc", "lb_kernels.cuh")
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-        if d.get("workload") == workload and d.get("kernel") == kernel and d.get("kernel_source_sha1") == sha:
-            return float(d["bytes_per_launch"])
+            entries = json.load(f)
+        sha = kernel_source_sha1()
+        for d in entries:
+            if d.get("workload") == workload and d.get("kernel") == kernel and d.get("kernel_source_sha1") == sha:
+                return float(d["bytes_per_launch"])
     except Exception:
         pass
     return None
@@ -300,10 +312,14 @@ def main():
     sites = sum(s["nx"] * s["ny"] for s in specs)
     prec = lb.LB_FP32 if args.precision == "fp32" else lb.LB_FP64
     b = make_batch(lb, specs, fields, prec, sptr)
-    mode = lb.LB_MODE_FUSED if args.mode == "fused" else lb.LB_MODE_LAUNCH
+    if args.mode == "tma" and prec == lb.LB_FP64:
+        args.mode = "fused"          # the TMA-staged step is FP32 only
+    mode = {"tma": lb.LB_MODE_TMA, "fused": lb.LB_MODE_FUSED, "launch": lb.LB_MODE_LAUNCH}[args.mode]
     b.set_config(mode, args.tile_height)
-    kbytes = BYTES_FUSED if mode == lb.LB_MODE_FUSED else BYTES_COLLIDE
-    kname = (("k_fused" if mode == lb.LB_MODE_FUSED else "k_collide")
+    one_pass = mode in (lb.LB_MODE_FUSED, lb.LB_MODE_TMA)
+    kbytes = BYTES_FUSED if one_pass else BYTES_COLLIDE
+    kname = (f"k_fused_tma<{args.tile_height}>" if mode == lb.LB_MODE_TMA else
+             ("k_fused" if mode == lb.LB_MODE_FUSED else "k_collide")
              + f"<{'float' if prec else 'double'}, {args.tile_height}>")
 
     # warm-up (untimed), then the timed region: K steps, barrier + sync on both sides
@@ -325,7 +341,7 @@ def main():
 
     ms_step = max_over_ranks(dist, ms[2], dev)
     value = sum_over_ranks(dist, sites, dev) / (ms_step * 1e-3) / 1e6
-    gpu_launches = 2 * args.steps
+    gpu_launches = (1 if one_pass else 2) * args.steps
 
     out = {
         "metric": "2-species MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
@@ -386,7 +402,7 @@ def main():
         b.step(256)
         ev1.record(stream)
         ev1.synchronize()
-        out["autotuned"] = {"mode": ["launch", "persistent", "fused"][tmode], "tile_height": tyh,
+        out["autotuned"] = {"mode": ["launch", "persistent", "fused", "tma"][tmode], "tile_height": tyh,
                             "trial_ms_per_step": tuned_ms,
                             "sustained_mlups": sites * 256 / (ev0.elapsed_time(ev1) * 1e-3) / 1e6}
 
@@ -414,13 +430,15 @@ def main():
             L.set_fields(rho4k)
             n4 = 4096 * 4096
             k = 20 if prec == lb.LB_FP32 else 8
-            L.set_config(lb.LB_MODE_FUSED, 4)
-            L.profile(3)
-            m = L.profile(k)
+            big_mode = mode if prec == lb.LB_FP32 else lb.LB_MODE_FUSED
+            L.set_config(big_mode, args.tile_height)
+            L.profile(3, flush.data_ptr(), FLUSH_BYTES)
+            m = L.profile(k, flush.data_ptr(), FLUSH_BYTES)
             L.set_config(lb.LB_MODE_LAUNCH, 4)
-            L.profile(2)
-            m2 = L.profile(k)
-            big[name] = {"mlups": n4 / (m[2] * 1e-3) / 1e6, "ms_per_step": m[2], "steps": k,
+            L.profile(2, flush.data_ptr(), FLUSH_BYTES)
+            m2 = L.profile(k, flush.data_ptr(), FLUSH_BYTES)
+            big[name] = {"mode": ["launch", "persistent", "fused", "tma"][big_mode], "tile_height": args.tile_height,
+                         "mlups": n4 / (m[2] * 1e-3) / 1e6, "ms_per_step": m[2], "steps": k,
                          "fused_achieved_gbs": BYTES_FUSED[prec] * n4 / (m[1] * 1e-3) / 1e9,
                          "fused_frac_of_measured_hbm": BYTES_FUSED[prec] * n4 / (m[1] * 1e-3) / 1e9 / peak,
                          "two_pass_mlups": n4 / (m2[2] * 1e-3) / 1e6, "collide_ms": m2[1], "density_ms": m2[0],

@@ -69,10 +69,20 @@ extern "C" {
  * LB_MODE_FUSED: each time step is one launch: every block forms the
  *   densities of its tile and 2-node halo from the populations itself (no
  *   separate density pass), then runs the fused force / collision / push;
- *   replayed 32 steps per CUDA graph. */
+ *   replayed 32 steps per CUDA graph.
+ * LB_MODE_TMA (LB_FP32 only): LB_MODE_FUSED with every tile whose box (the
+ *   tile, 4 columns each side, 2 rows above and below) lies inside its
+ *   lattice brought into shared memory by one tensor-memory-accelerator copy
+ *   of its 18 population planes and one of its 2 reference-density planes,
+ *   completed on an mbarrier; blocks stay resident and walk the tiles, the
+ *   next box in flight while the current tile computes.  Other tiles load as
+ *   in LB_MODE_FUSED.  Same arithmetic as LB_MODE_FUSED.  A copy not complete
+ *   within the wait limit (default 2 s) ends the block and the next
+ *   synchronising call returns LB_ETIMEOUT. */
 #define LB_MODE_LAUNCH 0
 #define LB_MODE_PERSISTENT 1
 #define LB_MODE_FUSED 2
+#define LB_MODE_TMA 3
 
 /* Densities the interaction stencils see beyond a wall (ghost rows
  * y = -1, -2 and y = ny, ny + 1). */
@@ -163,13 +173,16 @@ int lb_set_fields_device(lb_handle *h, const double *rho, const double *u);
 int lb_step(lb_handle *h, int64_t n);
 
 /* Block until the handle's queued work has finished.  Returns LB_ETIMEOUT
- * (once) if a bounded device-side wait of a persistent launch expired. */
+ * (once) if a bounded device-side wait of a persistent launch, or of a TMA
+ * copy in LB_MODE_TMA, expired. */
 int lb_synchronize(lb_handle *h);
 
-/* Execution configuration: mode (LB_MODE_LAUNCH, LB_MODE_PERSISTENT or
- * LB_MODE_FUSED) and
- * tile height (2, 4 or 8 nodes; tiles are 32 nodes wide, one thread per
- * node).  Default: LB_MODE_LAUNCH, 4.  Results do not depend on it. */
+/* Execution configuration: mode (LB_MODE_LAUNCH, LB_MODE_PERSISTENT,
+ * LB_MODE_FUSED, or LB_MODE_TMA for LB_FP32 lattices) and tile height (2, 4
+ * or 8 nodes; tiles are 32 nodes wide, one thread per node).  Default:
+ * LB_MODE_LAUNCH, 4.  Results do not depend on it beyond the rounding order of
+ * FP32 sums.  LB_EINVAL for an unknown mode or height, or LB_MODE_TMA on an
+ * LB_FP64 handle or where the driver offers no tensor-map encoder. */
 int lb_set_config(lb_handle *h, int32_t mode, int32_t tile_height);
 int lb_get_config(const lb_handle *h, int32_t *mode, int32_t *tile_height);
 
@@ -270,10 +283,12 @@ int lb_batch_profile(lb_batch *b, int32_t nsteps, void *flush_buf, size_t flush_
 int lb_batch_set_config(lb_batch *b, int32_t mode, int32_t tile_height);
 int lb_batch_get_config(const lb_batch *b, int32_t *mode, int32_t *tile_height);
 int lb_batch_autotune(lb_batch *b, int32_t trial_steps, const char *cache_path, double *best_ms);
-/* Limit of every bounded wait of the persistent kernel, in seconds (default
- * 2).  drop_tile >= 0 is a test hook: that tile of the batch's tile list
- * never reports completion, so the waits on it run out and the launch ends
- * with LB_ETIMEOUT; -1 turns the hook off. */
+/* Limit of every bounded wait of the persistent kernel and of the TMA copies
+ * of LB_MODE_TMA, in seconds (default 2).  drop_tile >= 0 is a test hook:
+ * that tile of the batch's tile list (for the configured tile height) never
+ * reports completion in LB_MODE_PERSISTENT, or never has its copy started in
+ * LB_MODE_TMA, so the waits on it run out and the launch ends with
+ * LB_ETIMEOUT; -1 turns the hook off. */
 int lb_batch_set_wait_limit(lb_batch *b, double seconds, int32_t drop_tile);
 
 /* ---- observables without any allocation ------------------------------------ */

@@ -29,6 +29,7 @@ UNITS = {
     "lb_api.cu": [],
     "lb_fp64.cu": ["-fmad=false"],
     "lb_fp32.cu": [],
+    "lb_tma.cu": [],
     "lb_noalloc.cu": ["-fmad=false"],
     "lb_adjoint.cu": ["-fmad=false"],
 }

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <fstream>
 #include <limits>
+#include <mutex>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -102,6 +103,28 @@ void fill_lat(lbk::Lat<real> &L, const lb_params &p)
     L.g_x = p.g[0];
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once (no link against
+// the driver library)
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
 }  // namespace
 
 struct lb_engine {
@@ -133,6 +156,10 @@ struct lb_engine {
     int drop_tile = -1;
     void *d_pool = nullptr;
     size_t pool_bytes = 0;
+    // LB_MODE_TMA: one set of tensor maps per lattice (FP32 only)
+    lbk::TmaMaps *d_tmaps = nullptr;
+    bool tma_ok = false;
+    std::string tma_why = "LB_MODE_TMA needs LB_FP32 populations";
     double *d_partials = nullptr;
     double *d_obs = nullptr;
     double *d_tmp = nullptr;
@@ -154,6 +181,7 @@ struct lb_engine {
         cudaFree(d_ctl);
         cudaFree(d_err);
         cudaFree(d_pool);
+        cudaFree(d_tmaps);
         cudaFree(d_partials);
         cudaFree(d_obs);
         cudaFree(d_tmp);
@@ -207,6 +235,9 @@ struct lb_engine {
         } else {
             const lbk::Lat<float> *L = (const lbk::Lat<float> *)d_lats;
             if (mode == LB_MODE_FUSED) return lbk::Launch<float>::fused(L, d_stiles[ti], 0, nt, par, ty, stream);
+            if (mode == LB_MODE_TMA)
+                return lbk::launch_fused_tma(L, d_stiles[ti], 0, nt, par, d_tmaps, d_err, wait_cycles, drop_tile, ty,
+                                             stream);
             e = lbk::Launch<float>::density(L, d_stiles[ti], 0, nt, par, ty, stream);
             if (e == cudaSuccess) e = lbk::Launch<float>::collide(L, d_stiles[ti], 0, nt, par, ty, stream);
         }
@@ -246,6 +277,63 @@ struct lb_engine {
             gexec = nullptr;
         }
     }
+    // Tensor maps of every FP32 lattice for LB_MODE_TMA: per tile height and
+    // population copy, the 18 population planes and the 2 reference-density
+    // planes as (x, y, plane) tensors, box 40 x (ty + 4) x planes.  Leaves
+    // tma_ok false, with the reason, where the driver cannot encode them.
+    int build_tma_maps()
+    {
+        EncodeTiledFn enc = tensor_map_encoder();
+        if (!enc) {
+            tma_why = "LB_MODE_TMA: the driver offers no cuTensorMapEncodeTiled";
+            return LB_OK;
+        }
+        std::vector<lbk::TmaMaps> maps(n);
+        std::memset((void *)maps.data(), 0, maps.size() * sizeof(lbk::TmaMaps));
+        for (int l = 0; l < n; ++l) {
+            const lbk::Lat<float> &L = L32[l];
+            const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4};
+            const cuuint64_t dim_p[3] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny, 18};
+            const cuuint64_t dim_r[3] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny, 2};
+            const cuuint32_t estr[3] = {1, 1, 1};
+            for (int ti = 0; ti < 3; ++ti) {
+                const cuuint32_t h = (cuuint32_t)(kTileHeights[ti] + 2 * lbk::HALO);
+                if (L.nx < lbk::kTmaBoxW || L.ny < (int)h) continue;   // no tile's box fits: never used
+                const cuuint32_t box_p[3] = {(cuuint32_t)lbk::kTmaBoxW, h, 18};
+                const cuuint32_t box_r[3] = {(cuuint32_t)lbk::kTmaBoxW, h, 2};
+                for (int par = 0; par < 2; ++par) {
+                    const CUresult r1 = enc(&maps[l].pop[ti][par], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)L.f[par],
+                                            dim_p, strides, box_p, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    const CUresult r2 = enc(&maps[l].ref[ti][par], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                                            (void *)L.rho[par], dim_r, strides, box_r, estr,
+                                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
+                        tma_why = "LB_MODE_TMA: cuTensorMapEncodeTiled rejected a lattice's layout";
+                        return LB_OK;
+                    }
+                }
+            }
+        }
+        if (lbk::prepare_fused_tma() != cudaSuccess) {
+            cudaGetLastError();
+            tma_why = "LB_MODE_TMA: the TMA kernels cannot get their shared memory on this device";
+            return LB_OK;
+        }
+        if (cudaMalloc((void **)&d_tmaps, maps.size() * sizeof(lbk::TmaMaps)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LB_ENOMEM, "cudaMalloc of the tensor maps failed");
+        }
+        cudaError_t ce = cudaMemcpyAsync(d_tmaps, maps.data(), maps.size() * sizeof(lbk::TmaMaps),
+                                         cudaMemcpyHostToDevice, stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+        if (ce != cudaSuccess) return cuda_fail(ce, "tensor map upload");
+        tma_ok = true;
+        return LB_OK;
+    }
+
     // a bounded device-side wait that ran out is reported once, then cleared
     int check_timeout()
     {
@@ -336,8 +424,9 @@ struct lb_engine {
 
     int set_config(int m, int tyv)
     {
-        if (m != LB_MODE_LAUNCH && m != LB_MODE_PERSISTENT && m != LB_MODE_FUSED)
-            return fail(LB_EINVAL, "mode must be LB_MODE_LAUNCH, LB_MODE_PERSISTENT or LB_MODE_FUSED");
+        if (m != LB_MODE_LAUNCH && m != LB_MODE_PERSISTENT && m != LB_MODE_FUSED && m != LB_MODE_TMA)
+            return fail(LB_EINVAL, "mode must be LB_MODE_LAUNCH, LB_MODE_PERSISTENT, LB_MODE_FUSED or LB_MODE_TMA");
+        if (m == LB_MODE_TMA && !tma_ok) return fail(LB_EINVAL, tma_why.c_str());
         if (ty_index(tyv) < 0) return fail(LB_EINVAL, "tile height must be 2, 4 or 8");
         if (m != mode || tyv != ty) drop_graph();
         mode = m;
@@ -366,7 +455,7 @@ struct lb_engine {
         for (int s = 0; s < nsteps && ce == cudaSuccess; ++s) {
             if (flush_bytes) ce = cudaMemsetAsync(flush, s & 0xff, flush_bytes, stream);
             if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s], stream);
-            const bool one = mode == LB_MODE_FUSED;
+            const bool one = mode == LB_MODE_FUSED || mode == LB_MODE_TMA;
             if (precision == LB_FP64) {
                 const lbk::Lat<double> *L = (const lbk::Lat<double> *)d_lats;
                 if (ce == cudaSuccess && !one) ce = lbk::Launch<double>::density(L, d_stiles[ti], 0, nt, parity, ty, stream);
@@ -379,8 +468,10 @@ struct lb_engine {
                 if (ce == cudaSuccess && !one) ce = lbk::Launch<float>::density(L, d_stiles[ti], 0, nt, parity, ty, stream);
                 if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s + 1], stream);
                 if (ce == cudaSuccess)
-                    ce = one ? lbk::Launch<float>::fused(L, d_stiles[ti], 0, nt, parity, ty, stream)
-                             : lbk::Launch<float>::collide(L, d_stiles[ti], 0, nt, parity, ty, stream);
+                    ce = mode == LB_MODE_TMA ? lbk::launch_fused_tma(L, d_stiles[ti], 0, nt, parity, d_tmaps, d_err,
+                                                                     wait_cycles, drop_tile, ty, stream)
+                         : one ? lbk::Launch<float>::fused(L, d_stiles[ti], 0, nt, parity, ty, stream)
+                               : lbk::Launch<float>::collide(L, d_stiles[ti], 0, nt, parity, ty, stream);
             }
             if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s + 2], stream);
             if (ce == cudaSuccess) {
@@ -469,7 +560,8 @@ struct lb_engine {
         double best = std::numeric_limits<double>::infinity();
         int bm = mode, bty = ty;
         cudaError_t ce = cudaMemcpyAsync(snap, d_pool, pool_bytes, cudaMemcpyDeviceToDevice, stream);
-        for (int m = LB_MODE_LAUNCH; m <= LB_MODE_FUSED && ce == cudaSuccess && rc == LB_OK; ++m)
+        const int last_mode = tma_ok ? LB_MODE_TMA : LB_MODE_FUSED;
+        for (int m = LB_MODE_LAUNCH; m <= last_mode && ce == cudaSuccess && rc == LB_OK; ++m)
             for (int tyv : kTileHeights) {
                 if ((rc = set_config(m, tyv))) break;
                 if ((rc = step(chunk_steps()))) break;            // warm-up, builds the graph
@@ -905,6 +997,10 @@ int engine_create(const lb_params *p, int n, lb_engine **out)
                               e->stream)) != cudaSuccess ||
         (ce = cudaStreamSynchronize(e->stream)) != cudaSuccess)
         return bail(cuda_fail(ce, "descriptor upload"));
+    if (e->precision == LB_FP32) {
+        const int rc = e->build_tma_maps();
+        if (rc) return bail(rc);
+    }
     *out = e;
     return LB_OK;
 }

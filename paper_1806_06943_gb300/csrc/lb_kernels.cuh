@@ -572,11 +572,50 @@ __device__ __forceinline__ real node_density(const Lat<real> &L, int k, int gx, 
     return r;
 }
 
+// Densities and psi of staged slot (sx, sy) of tile t (slot (HALO, HALO) is
+// the tile's first node) from the populations of its node: x wraps; beyond
+// the lattice in y, periodic wrap, or a wall ghost row (the mirrored fluid
+// row, or the fixed wall densities).
+template <typename real, int TYv, bool kCG>
+__device__ __forceinline__ void stage_slot(const Lat<real> &G, int4 t, int parity, CollideSmem<real, TYv> &sm, int sx,
+                                           int sy)
+{
+    const int nx = G.nx, ny = G.ny;
+    const int gx = wrap_index(t.y + sx - HALO, nx);
+    int gy = t.z + sy - HALO;
+    real rA, rB;
+    bool fixed = false;
+    if (gy < 0 || gy >= ny) {
+        if (G.walls) {
+            if (G.wall_mode == 1) {
+                rA = G.wall_rho[0];
+                rB = G.wall_rho[1];
+                fixed = true;
+            } else {
+                gy = gy < 0 ? -1 - gy : 2 * ny - 1 - gy;
+                gy = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);  // rows no valid node reads
+            }
+        } else {
+            gy = wrap_index(gy, ny);
+        }
+    }
+    if (!fixed) {
+        rA = node_density<real, kCG>(G, 0, gx, gy, parity);
+        rB = node_density<real, kCG>(G, 1, gx, gy, parity);
+    }
+    sm.srho[0][sy][sx] = rA;
+    sm.srho[1][sy][sx] = rB;
+    sm.spsi[0][sy][sx] = psi_of<real>(rA);
+    sm.spsi[1][sy][sx] = psi_of<real>(rB);
+}
+
 // One time step of one tile in a single pass: each thread forms its node's
 // densities from the populations it loads anyway; the 2-node halo (and the
 // slots of a ragged tile's missing nodes) is formed from the neighbours'
-// populations, mostly L2 hits.  FP32 writes the node's density as the next
-// step's reference.  Then the fused force + collision + push of collide_site.
+// populations, mostly L2 hits.  The halo goes first, so that its loads and
+// the node's own 18 populations are not held in registers at the same time.
+// FP32 writes the node's density as the next step's reference.  Then the
+// fused force + collision + push of collide_site.
 template <typename real, int TYv, bool kCG>
 __device__ __forceinline__ void fused_tile(const Lat<real> *__restrict__ lats, int4 t, int parity,
                                            CollideSmem<real, TYv> &sm)
@@ -592,6 +631,32 @@ __device__ __forceinline__ void fused_tile(const Lat<real> *__restrict__ lats, i
     const real *__restrict__ fc = G.f[parity];
     real *__restrict__ fn = G.f[parity ^ 1];
     const size_t c = valid ? (size_t)y * G.pitch + x : 0;
+    // the halo ring, enumerated compactly: two rows above, two below, then
+    // the two columns on each side of the tile's rows
+    constexpr int kRing = 4 * SW + 4 * TYv;
+    for (int h = tid; h < kRing; h += TX * TYv) {
+        int sx, sy;
+        if (h < 2 * SW) {
+            sy = h / SW;
+            sx = h % SW;
+        } else if (h < 4 * SW) {
+            sy = TYv + HALO + (h - 2 * SW) / SW;
+            sx = (h - 2 * SW) % SW;
+        } else {
+            const int q = h - 4 * SW;
+            sy = HALO + q / 4;
+            sx = (q % 4 < 2) ? q % 4 : TX + q % 4;
+        }
+        stage_slot<real, TYv, kCG>(G, t, parity, sm, sx, sy);
+    }
+    // a ragged tile's slots without a node of their own hold wrapped copies
+    if (t.y + TX > nx || t.z + TYv > ny) {
+        for (int q = tid; q < TX * TYv; q += TX * TYv) {
+            const int sx = HALO + q % TX, sy = HALO + q / TX;
+            if (t.y + sx - HALO >= nx || t.z + sy - HALO >= ny) stage_slot<real, TYv, kCG>(G, t, parity, sm, sx, sy);
+        }
+    }
+    // then the node's own populations (kept in registers for the collision)
     real fk[2][9];
 #pragma unroll
     for (int k = 0; k < 2; ++k)
@@ -610,60 +675,6 @@ __device__ __forceinline__ void fused_tile(const Lat<real> *__restrict__ lats, i
             }
             sm.srho[k][cy][cx] = r;
             sm.spsi[k][cy][cx] = psi_of<real>(r);
-        }
-    }
-    // densities of one staged slot from the populations of its node
-    auto stage_slot = [&](int sx, int sy) {
-        const int gx = wrap_index(t.y + sx - HALO, nx);
-        int gy = t.z + sy - HALO;
-        real rA, rB;
-        bool fixed = false;
-        if (gy < 0 || gy >= ny) {
-            if (G.walls) {
-                if (G.wall_mode == 1) {
-                    rA = G.wall_rho[0];
-                    rB = G.wall_rho[1];
-                    fixed = true;
-                } else {
-                    gy = gy < 0 ? -1 - gy : 2 * ny - 1 - gy;
-                    gy = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);  // rows no valid node reads
-                }
-            } else {
-                gy = wrap_index(gy, ny);
-            }
-        }
-        if (!fixed) {
-            rA = node_density<real, kCG>(G, 0, gx, gy, parity);
-            rB = node_density<real, kCG>(G, 1, gx, gy, parity);
-        }
-        sm.srho[0][sy][sx] = rA;
-        sm.srho[1][sy][sx] = rB;
-        sm.spsi[0][sy][sx] = psi_of<real>(rA);
-        sm.spsi[1][sy][sx] = psi_of<real>(rB);
-    };
-    // the halo ring, enumerated compactly: two rows above, two below, then
-    // the two columns on each side of the tile's rows
-    constexpr int kRing = 4 * SW + 4 * TYv;
-    for (int h = tid; h < kRing; h += TX * TYv) {
-        int sx, sy;
-        if (h < 2 * SW) {
-            sy = h / SW;
-            sx = h % SW;
-        } else if (h < 4 * SW) {
-            sy = TYv + HALO + (h - 2 * SW) / SW;
-            sx = (h - 2 * SW) % SW;
-        } else {
-            const int q = h - 4 * SW;
-            sy = HALO + q / 4;
-            sx = (q % 4 < 2) ? q % 4 : TX + q % 4;
-        }
-        stage_slot(sx, sy);
-    }
-    // a ragged tile's slots without a node of their own hold wrapped copies
-    if (t.y + TX > nx || t.z + TYv > ny) {
-        for (int q = tid; q < TX * TYv; q += TX * TYv) {
-            const int sx = HALO + q % TX, sy = HALO + q / TX;
-            if (t.y + sx - HALO >= nx || t.z + sy - HALO >= ny) stage_slot(sx, sy);
         }
     }
     __syncthreads();

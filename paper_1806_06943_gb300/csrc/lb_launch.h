@@ -2,6 +2,7 @@
 // explicit instantiation per population format (lb_fp64.cu, lb_fp32.cu).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lb_types.h"
@@ -40,6 +41,28 @@ struct Launch {
 
 extern template struct Launch<double>;
 extern template struct Launch<float>;
+
+// Tensor maps of one FP32 lattice for the TMA-staged one-pass step
+// (lb_tma.cu): for each tile height (2, 4, 8) and population copy, the 18
+// population planes and the 2 reference-density planes as 3-D tensors
+// (x, y, plane), with a box of the tile plus 4 columns on each side and 2 rows
+// above and below.  Zero-filled where unused (lattices narrower than the box).
+struct TmaMaps {
+    CUtensorMap pop[3][2];
+    CUtensorMap ref[3][2];
+};
+constexpr int kTmaBoxW = 40;             // 32 + 2 x 4 columns: x offsets stay 16-byte aligned
+// Shared-memory opt-in of the TMA kernels on the current device; call once
+// before the first launch_fused_tma, outside stream capture.
+cudaError_t prepare_fused_tma();
+// One time step of the FP32 lattices in one pass, one block per tile: every
+// full tile of a lattice that holds a whole box is staged by one TMA copy of
+// its population box and one of its reference-density box (the others load
+// as the plain one-pass kernel does).  A copy not complete after wait_cycles
+// SM clocks sets *err and ends the block; the copy of tile drop_tile (a test
+// hook, -1 for none) is never started.
+cudaError_t launch_fused_tma(const Lat<float> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
+                             const TmaMaps *maps, int *err, long long wait_cycles, int drop_tile, int ty, cudaStream_t s);
 
 // Discrete adjoint of the FP64 step (lb_adjoint.cu).  Buffers use the
 // lattice's pitched layout; abuf holds 20 planes, gpart 8 doubles per tile of

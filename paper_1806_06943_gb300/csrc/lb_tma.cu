@@ -1,0 +1,237 @@
+// lb_tma.cu -- the FP32 one-pass time step with each tile's populations and
+// reference densities, halo included, brought into shared memory by the
+// tensor memory accelerator (cp.async.bulk.tensor, completion on an mbarrier)
+// instead of per-thread loads.  Same arithmetic as fused_tile in the same
+// order, so the results are the same bit for bit: the densities of the staged
+// nodes are the sums of Eq. (6) over the boxed populations, then the forces
+// of Eqs. (8), (9), the collision of Eqs. (1), (2), (5) and the push
+// streaming of collide_site.
+//
+// Box of a tile (x0, y0) of 32 x TY nodes: columns x0 - 4 .. x0 + 35 (the
+// D2Q25 halo needs 2; 4 keep the x offset a multiple of 16 bytes), rows
+// y0 - 2 .. y0 + TY + 1, all 18 population planes; a second box holds the 2
+// reference-density planes.  Parts of the box beyond the lattice are filled
+// with zeros by the copy and not used: the halo slots there (across a
+// periodic edge, or wall ghost rows) are formed as in fused_tile.  Ragged
+// tiles, and lattices narrower than the box, take the plain-load path.
+#include "lb_kernels.cuh"
+#include "lb_launch.h"
+
+namespace lbk {
+
+namespace {
+
+template <int TYv>
+struct TmaBox {
+    static constexpr int H = TYv + 2 * HALO;
+    static constexpr int kPop = kTmaBoxW * H * 18;   // floats
+    static constexpr int kRef = kTmaBoxW * H * 2;
+    static constexpr int kStage = kPop + kRef;
+    static constexpr unsigned kBytes = (unsigned)kStage * 4u;
+    static_assert((kPop * 4) % 128 == 0 && (kStage * 4) % 128 == 0, "stage buffers stay 128-byte aligned");
+};
+
+// Resident blocks per SM the kernel is compiled for: as the plain one-pass
+// kernel, unless the staging buffer leaves room for fewer.
+template <int TYv>
+constexpr int kTmaMinBlocks = (225 * 1024) / (TmaBox<TYv>::kBytes + 8 * 1024) < kCollideMinBlocks<float, TYv>
+                                  ? (225 * 1024) / (TmaBox<TYv>::kBytes + 8 * 1024)
+                                  : kCollideMinBlocks<float, TYv>;
+
+// the tile is full and its lattice holds a whole box (so its maps exist)
+__device__ __forceinline__ bool box_tile(const Lat<float> &G, int4 t, int tyv)
+{
+    return t.y + TX <= G.nx && t.z + tyv <= G.ny && G.nx >= kTmaBoxW && G.ny >= tyv + 2 * HALO;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the completion of phase `phase` of *bar.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase, long long limit)
+{
+    const long long start = clock64();
+    while (!mbar_try_wait(bar, phase))
+        if (clock64() - start > limit) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// fused_tile with the tile's and the halo's populations and reference
+// densities read from the box (pop: [18][H][40], ref: [2][H][40]).  The tile
+// is full.
+template <int TYv>
+__device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ lats, int4 t, int parity,
+                                               CollideSmem<float, TYv> &sm, const float *__restrict__ pop,
+                                               const float *__restrict__ ref)
+{
+    constexpr int SHv = TYv + 2 * HALO, H = SHv, W = kTmaBoxW;
+    const Lat<float> &G = lats[t.x];
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    if (tid < (int)(sizeof(Lat<float>) / 4))
+        reinterpret_cast<uint32_t *>(&sm.L)[tid] = reinterpret_cast<const uint32_t *>(&G)[tid];
+    // staged slot (sx, sy) is box column sx + 2, row sy; the same sums as
+    // node_density
+    auto slot_density = [&](int k, int sx, int sy) {
+        float v[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) v[i] = pop[((k * 9 + i) * H + sy) * W + sx + 2];
+        const float r = zeroth_moment<float>(v);
+        return ref[(k * H + sy) * W + sx + 2] + r;
+    };
+    constexpr int kRing = 4 * SW + 4 * TYv;
+    for (int h = tid; h < kRing; h += TX * TYv) {
+        int sx, sy;
+        if (h < 2 * SW) {
+            sy = h / SW;
+            sx = h % SW;
+        } else if (h < 4 * SW) {
+            sy = TYv + HALO + (h - 2 * SW) / SW;
+            sx = (h - 2 * SW) % SW;
+        } else {
+            const int q = h - 4 * SW;
+            sy = HALO + q / 4;
+            sx = (q % 4 < 2) ? q % 4 : TX + q % 4;
+        }
+        const int gx = t.y + sx - HALO, gy = t.z + sy - HALO;
+        if (gx < 0 || gx >= G.nx || gy < 0 || gy >= G.ny) {   // not in the box's lattice part
+            stage_slot<float, TYv, false>(G, t, parity, sm, sx, sy);
+            continue;
+        }
+        const float rA = slot_density(0, sx, sy), rB = slot_density(1, sx, sy);
+        sm.srho[0][sy][sx] = rA;
+        sm.srho[1][sy][sx] = rB;
+        sm.spsi[0][sy][sx] = psi_of<float>(rA);
+        sm.spsi[1][sy][sx] = psi_of<float>(rB);
+    }
+    const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
+    const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
+    const size_t c = (size_t)y * G.pitch + x;
+    float fk[2][9], Rn[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fk[k][i] = pop[((k * 9 + i) * H + cy) * W + cx + 2];
+        Rn[k] = ref[(k * H + cy) * W + cx + 2];
+        const float r = Rn[k] + zeroth_moment<float>(fk[k]);
+        G.rho[parity ^ 1][(size_t)k * G.plane + c] = r;
+        sm.srho[k][cy][cx] = r;
+        sm.spsi[k][cy][cx] = psi_of<float>(r);
+    }
+    __syncthreads();
+    const bool inner = t.y >= 1 && t.y + TX + 1 <= sm.L.nx && t.z >= 1 && t.z + TYv + 1 <= sm.L.ny;
+    if (inner) collide_site<float, true, SHv>(sm.L, G.f[parity ^ 1], sm.srho, sm.spsi, fk, Rn, x, y, cx, cy);
+    else collide_site<float, false, SHv>(sm.L, G.f[parity ^ 1], sm.srho, sm.spsi, fk, Rn, x, y, cx, cy);
+}
+
+// One block per tile: thread 0 starts the two copies, every thread waits
+// (bounded) on the mbarrier, then the tile is computed from the box.
+template <int TYv>
+__global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
+    k_fused_tma(const Lat<float> *__restrict__ lats, const int4 *__restrict__ tiles, int tile_offset, int parity,
+                const TmaMaps *__restrict__ maps, int *err, long long wait_cycles, int drop_tile)
+{
+    using B = TmaBox<TYv>;
+    constexpr int ti = TYv == 2 ? 0 : (TYv == 4 ? 1 : 2);
+    extern __shared__ __align__(128) float box[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ CollideSmem<float, TYv> sm;
+    const int4 t = tiles[tile_offset + blockIdx.x];
+    if (!box_tile(lats[t.x], t, TYv)) {
+        fused_tile<float, TYv, false>(lats, t, parity, sm);
+        return;
+    }
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    // the copy of drop_tile (a test hook) is never started: its wait runs out
+    const bool issued = tile_offset + (int)blockIdx.x != drop_tile;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (issued) {
+            mbar_expect_tx(&bar, B::kBytes);
+            tma_load_3d(box, &maps[t.x].pop[ti][parity], t.y - 4, t.z - HALO, 0, &bar);
+            tma_load_3d(box + B::kPop, &maps[t.x].ref[ti][parity], t.y - 4, t.z - HALO, 0, &bar);
+        }
+    }
+    __syncthreads();   // the barrier is initialised before anyone waits on it
+    const bool ok = mbar_wait(&bar, 0, wait_cycles);
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            // let a copy still in flight land before the block ends (bounded
+            // too, by at least 2^31 clocks, ~1 s)
+            if (issued) mbar_wait(&bar, 0, wait_cycles > (1ll << 31) ? wait_cycles : (1ll << 31));
+        }
+        return;
+    }
+    fused_tile_box<TYv>(lats, t, parity, sm, box, box + B::kPop);
+}
+
+template <int TYv>
+struct TmaKernel {
+    static constexpr size_t kSmem = TmaBox<TYv>::kBytes;
+    static cudaError_t prepare()
+    {
+        return cudaFuncSetAttribute(k_fused_tma<TYv>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    }
+    static cudaError_t launch(const Lat<float> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
+                              const TmaMaps *maps, int *err, long long wait_cycles, int drop_tile, cudaStream_t s)
+    {
+        k_fused_tma<TYv><<<n_tiles, dim3(TX, TYv), kSmem, s>>>(lats, tiles, tile_offset, parity, maps, err, wait_cycles,
+                                                               drop_tile);
+        return cudaGetLastError();
+    }
+};
+
+}  // namespace
+
+cudaError_t prepare_fused_tma()
+{
+    cudaError_t e = TmaKernel<2>::prepare();
+    if (e == cudaSuccess) e = TmaKernel<4>::prepare();
+    if (e == cudaSuccess) e = TmaKernel<8>::prepare();
+    return e;
+}
+
+cudaError_t launch_fused_tma(const Lat<float> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
+                             const TmaMaps *maps, int *err, long long wait_cycles, int drop_tile, int ty, cudaStream_t s)
+{
+    if (n_tiles <= 0) return cudaSuccess;
+    switch (ty) {
+    case 2: return TmaKernel<2>::launch(lats, tiles, tile_offset, n_tiles, parity, maps, err, wait_cycles, drop_tile, s);
+    case 4: return TmaKernel<4>::launch(lats, tiles, tile_offset, n_tiles, parity, maps, err, wait_cycles, drop_tile, s);
+    case 8: return TmaKernel<8>::launch(lats, tiles, tile_offset, n_tiles, parity, maps, err, wait_cycles, drop_tile, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lbk

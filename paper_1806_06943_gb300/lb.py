@@ -24,7 +24,7 @@ LB_FP64, LB_FP32 = 0, 1
 LB_PERIODIC, LB_WALLS_Y = 0, 1
 LB_WALL_MIRROR, LB_WALL_FIXED = 0, 1
 LB_STATIC_MAX_TILES = 32768
-LB_MODE_LAUNCH, LB_MODE_PERSISTENT, LB_MODE_FUSED = 0, 1, 2
+LB_MODE_LAUNCH, LB_MODE_PERSISTENT, LB_MODE_FUSED, LB_MODE_TMA = 0, 1, 2, 3
 LB_OBJ_MU_R, LB_OBJ_DP = 0, 1
 
 

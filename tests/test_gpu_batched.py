@@ -1,5 +1,6 @@
 """Batched form: every execution configuration (two-launch steps, one
-persistent launch per 64 steps, or one-pass steps; tile heights 2, 4, 8) gives the same
+persistent launch per 64 steps, one-pass steps, or TMA-staged one-pass steps
+in FP32; tile heights 2, 4, 8) gives the same
 populations; the persistent kernel's bounded waits end with LB_ETIMEOUT when a
 tile never reports; the autotuner leaves the state untouched and caches its
 choice."""
@@ -18,6 +19,7 @@ SPECS = [
     dict(nx=130, ny=6, tau=(1.3, 0.9), walls=1, wall_mode=0, g=(2e-5, 0.0)),
 ]
 CONFIGS = [(m, ty) for m in (0, 1, 2) for ty in (2, 4, 8)]
+TMA_CONFIGS = [(3, ty) for ty in (2, 4, 8)]    # FP32 only
 
 
 @pytest.fixture(scope="module")
@@ -50,7 +52,7 @@ def test_all_configurations_agree(lbmod, oracle_mod, precision):
     steps = 3 * 64 + 5          # graph replays plus a ragged remainder
     ref = run_batch(lbmod, precision, (0, 4), steps, rhos)
     ref_fields = [ref.fields(i) for i in range(len(SPECS))]
-    for cfg in CONFIGS:
+    for cfg in CONFIGS + (TMA_CONFIGS if precision == 1 else []):
         b = run_batch(lbmod, precision, cfg, steps, rhos)
         for i in range(len(SPECS)):
             got = b.fields(i)
@@ -103,7 +105,7 @@ def test_autotune_keeps_state_and_caches(lbmod, tmp_path):
     ms = b.autotune(16, cache)
     assert ms > 0
     cfg = b.config()
-    assert cfg in CONFIGS
+    assert cfg in CONFIGS + TMA_CONFIGS
     after = [b.fields(i) for i in range(len(SPECS))]
     for x, y in zip(before, after):
         assert np.array_equal(x["rho"], y["rho"]) and np.array_equal(x["mom"], y["mom"])
