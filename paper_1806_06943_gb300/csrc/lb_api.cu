@@ -156,8 +156,12 @@ struct lb_engine {
     int drop_tile = -1;
     void *d_pool = nullptr;
     size_t pool_bytes = 0;
-    // LB_MODE_TMA: one set of tensor maps per lattice (FP32 only)
+    // LB_MODE_TMA: one set of tensor maps per lattice (FP32 only), and per
+    // tile height the time-step tiles reordered: the n_box tiles staged by TMA
+    // first, then the others
     lbk::TmaMaps *d_tmaps = nullptr;
+    int4 *d_btiles[3] = {nullptr, nullptr, nullptr};
+    int n_box[3] = {0, 0, 0};
     bool tma_ok = false;
     std::string tma_why = "LB_MODE_TMA needs LB_FP32 populations";
     double *d_partials = nullptr;
@@ -177,6 +181,7 @@ struct lb_engine {
         for (int i = 0; i < 3; ++i) {
             cudaFree(d_stiles[i]);
             cudaFree(d_sntiles[i]);
+            cudaFree(d_btiles[i]);
         }
         cudaFree(d_ctl);
         cudaFree(d_err);
@@ -235,12 +240,20 @@ struct lb_engine {
         } else {
             const lbk::Lat<float> *L = (const lbk::Lat<float> *)d_lats;
             if (mode == LB_MODE_FUSED) return lbk::Launch<float>::fused(L, d_stiles[ti], 0, nt, par, ty, stream);
-            if (mode == LB_MODE_TMA)
-                return lbk::launch_fused_tma(L, d_stiles[ti], 0, nt, par, d_tmaps, d_err, wait_cycles, drop_tile, ty,
-                                             stream);
+            if (mode == LB_MODE_TMA) return launch_tma(L, ti, nt, par);
             e = lbk::Launch<float>::density(L, d_stiles[ti], 0, nt, par, ty, stream);
             if (e == cudaSuccess) e = lbk::Launch<float>::collide(L, d_stiles[ti], 0, nt, par, ty, stream);
         }
+        return e;
+    }
+    // LB_MODE_TMA step: the TMA kernel over the box tiles, the plain one-pass
+    // kernel over the rest
+    cudaError_t launch_tma(const lbk::Lat<float> *L, int ti, int nt, int par)
+    {
+        cudaError_t e = lbk::launch_fused_tma(L, d_btiles[ti], 0, n_box[ti], par, d_tmaps, d_err, wait_cycles, drop_tile,
+                                              ty, stream);
+        if (e == cudaSuccess && nt > n_box[ti])
+            e = lbk::Launch<float>::fused(L, d_btiles[ti], n_box[ti], nt - n_box[ti], par, ty, stream);
         return e;
     }
     size_t ctl_bytes() const { return 8 + 2 * sizeof(unsigned) * (size_t)n; }
@@ -330,6 +343,21 @@ struct lb_engine {
                                          cudaMemcpyHostToDevice, stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
         if (ce != cudaSuccess) return cuda_fail(ce, "tensor map upload");
+        for (int ti = 0; ti < 3; ++ti) {
+            const int tyv = kTileHeights[ti];
+            std::vector<int4> box, rest;
+            for (const int4 &t : stiles[ti])
+                (lbk::tma_box_tile(P[t.x].nx, P[t.x].ny, t.y, t.z, tyv) ? box : rest).push_back(t);
+            n_box[ti] = (int)box.size();
+            box.insert(box.end(), rest.begin(), rest.end());
+            if (cudaMalloc((void **)&d_btiles[ti], box.size() * sizeof(int4)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(LB_ENOMEM, "cudaMalloc of the TMA tile lists failed");
+            }
+            ce = cudaMemcpyAsync(d_btiles[ti], box.data(), box.size() * sizeof(int4), cudaMemcpyHostToDevice, stream);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+            if (ce != cudaSuccess) return cuda_fail(ce, "TMA tile list upload");
+        }
         tma_ok = true;
         return LB_OK;
     }
@@ -343,7 +371,8 @@ struct lb_engine {
         if (h) {
             LB_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), stream));
             LB_CUDA(cudaStreamSynchronize(stream));
-            return fail(LB_ETIMEOUT, "a bounded wait of the persistent kernel expired; the state is invalid");
+            if (h == 2) return fail(LB_ECUDA, "internal: a tile of the TMA list is not a box tile; the state is invalid");
+            return fail(LB_ETIMEOUT, "a bounded device-side wait expired (persistent kernel or TMA copy); the state is invalid");
         }
         return LB_OK;
     }
@@ -468,8 +497,7 @@ struct lb_engine {
                 if (ce == cudaSuccess && !one) ce = lbk::Launch<float>::density(L, d_stiles[ti], 0, nt, parity, ty, stream);
                 if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * s + 1], stream);
                 if (ce == cudaSuccess)
-                    ce = mode == LB_MODE_TMA ? lbk::launch_fused_tma(L, d_stiles[ti], 0, nt, parity, d_tmaps, d_err,
-                                                                     wait_cycles, drop_tile, ty, stream)
+                    ce = mode == LB_MODE_TMA ? launch_tma(L, ti, nt, parity)
                          : one ? lbk::Launch<float>::fused(L, d_stiles[ti], 0, nt, parity, ty, stream)
                                : lbk::Launch<float>::collide(L, d_stiles[ti], 0, nt, parity, ty, stream);
             }

@@ -302,9 +302,11 @@ struct SpeciesTerms {
     real dg[2];        // sum_i of the offsets from rho_k: minus the rounding of rho_k
 };
 
+// Collision and push of direction I of both species, fI[k] the node's
+// population (FP32: its offset) of that direction.
 template <typename real, int I, bool kInner, int SHv>
 __device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW],
-                                                 const real (&fk)[2][9], const real (&rho)[2], real ux, real uy, real uu,
+                                                 const real (&fI)[2], const real (&rho)[2], real ux, real uy, real uu,
                                                  const real (&F)[2][2], const SpeciesTerms<real> &st, int x, int y,
                                                  int cx, int cy)
 {
@@ -312,7 +314,7 @@ __device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__res
         (void)st;
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const real v = collide_dir<real, I>(fk[k][I], rho[k], ux, uy, uu, F[k][0], F[k][1], L.omega[k],
+            const real v = collide_dir<real, I>(fI[k], rho[k], ux, uy, uu, F[k][0], F[k][1], L.omega[k],
                                                 L.aw[k][cls9(I)]);
             push_dir<real, I, kInner, SHv>(L, fn, srho, k, x, y, cx, cy, v);
         }
@@ -331,7 +333,7 @@ __device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__res
             // the equilibrium carries the node's exact mass: its offsets from the
             // rounded rho_k sum to dg, like the populations' do
             const real geq = st.wr[k][C] * q + (real)w9(I) * st.dg[k];
-            const real f = fk[k][I];
+            const real f = fI[k];
             const real v = (f + L.omega[k] * (geq - f)) + Cg;
             push_dir<real, I, kInner, SHv>(L, fn, srho, k, x, y, cx, cy, v);
         }
@@ -410,10 +412,11 @@ struct CollideSmem {
     Lat<real> L;   // descriptor copy: stores to the populations cannot alias it
 };
 
-template <typename real, bool kInner, int SHv>
+template <typename real, bool kInner, int SHv, bool kBox = false>
 __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW],
                                              const real (*spsi)[SHv][SW], real (&fk)[2][9], const real (&Rn)[2], int x,
-                                             int y, int cx, int cy);
+                                             int y, int cx, int cy, const real *__restrict__ box = nullptr,
+                                             int box_plane = 0);
 
 // Fused force + collision + push-streaming + bounce-back for one tile.  Every
 // thread of the block calls it and returns from it; it ends after the tile's
@@ -498,18 +501,30 @@ __global__ void __launch_bounds__(TX *TYv, kCollideMinBlocks<real, TYv>)
     collide_tile<real, TYv, false>(lats, tiles[tile_offset + blockIdx.x], parity, sm);
 }
 
-template <typename real, bool kInner, int SHv>
+// Force, moments, u^eq, collision and push of the node (x, y), staged at
+// (cx, cy).  Its populations are fk (updated in place), or with kBox (FP32)
+// the shared-memory box: box[(k * 9 + i) * box_plane] is population i of
+// species k, read again where it is used with the same density offset
+// applied, which keeps 18 registers free; fk is then not used.
+template <typename real, bool kInner, int SHv, bool kBox>
 __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW],
                                              const real (*spsi)[SHv][SW], real (&fk)[2][9], const real (&Rn)[2], int x,
-                                             int y, int cx, int cy)
+                                             int y, int cx, int cy, const real *__restrict__ box, int box_plane)
 {
-    real F[2][2], rho[2], m[2][2], dg[2] = {(real)0, (real)0};
+    static_assert(!kBox || kOffset<real>, "the box form is FP32 only");
+    real F[2][2], rho[2], m[2][2], dg[2] = {(real)0, (real)0}, delta[2] = {(real)0, (real)0};
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         force_at<real, SHv>(L, srho, spsi, k, cx, cy, F[k][0], F[k][1]);
         rho[k] = srho[k][cy][cx];
+        real fb[9];
+        if constexpr (kBox) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fb[i] = box[(k * 9 + i) * box_plane];
+        }
+        real(&f)[9] = kBox ? fb : fk[k];
         real jx, jy;
-        first_moment<real>(fk[k], jx, jy);     // FP32: the reference density adds no momentum
+        first_moment<real>(f, jx, jy);     // FP32: the reference density adds no momentum
         m[k][0] = jx + (real)0.5 * F[k][0];   // Eq. (6), half force
         m[k][1] = jy + (real)0.5 * F[k][1];
         if constexpr (kOffset<real>) {
@@ -518,10 +533,10 @@ __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restric
             // are close), so f = h + w R is kept exactly whatever rho rounded to;
             // with sum_i h_i instead, density changes below half an ulp of R
             // would be dropped at every step and mass would drift.
-            const real delta = rho[k] - Rn[k];
+            delta[k] = rho[k] - Rn[k];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) fk[k][i] -= (real)w9(i) * delta;
-            dg[k] = zeroth_moment<real>(fk[k]);
+            for (int i = 0; i < 9; ++i) f[i] -= (real)w9(i) * delta[k];
+            dg[k] = zeroth_moment<real>(f);
         }
     }
     // common velocity, Eq. (3)
@@ -544,15 +559,38 @@ __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restric
         }
     }
 
-    collide_push_dir<real, 0, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 1, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 2, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 3, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 4, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 5, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 6, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 7, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    collide_push_dir<real, 8, kInner, SHv>(L, fn, srho, fk, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    // the population of direction I of both species, as the moments saw it
+    auto dir_pops = [&](int I, real(&fI)[2]) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if constexpr (kBox) {
+                real h = box[(k * 9 + I) * box_plane];
+                h -= (real)w9(I) * delta[k];
+                fI[k] = h;
+            } else {
+                fI[k] = fk[k][I];
+            }
+        }
+    };
+    real fI[2];
+    dir_pops(0, fI);
+    collide_push_dir<real, 0, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    dir_pops(1, fI);
+    collide_push_dir<real, 1, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    dir_pops(2, fI);
+    collide_push_dir<real, 2, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    dir_pops(3, fI);
+    collide_push_dir<real, 3, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    dir_pops(4, fI);
+    collide_push_dir<real, 4, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    dir_pops(5, fI);
+    collide_push_dir<real, 5, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    dir_pops(6, fI);
+    collide_push_dir<real, 6, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    dir_pops(7, fI);
+    collide_push_dir<real, 7, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    dir_pops(8, fI);
+    collide_push_dir<real, 8, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
 }
 
 // ---- one-pass step ------------------------------------------------------------

@@ -52,15 +52,22 @@ struct TmaMaps {
     CUtensorMap ref[3][2];
 };
 constexpr int kTmaBoxW = 40;             // 32 + 2 x 4 columns: x offsets stay 16-byte aligned
+// The tile (x0, y0) of height ty of an nx x ny lattice is staged by TMA.
+__host__ __device__ inline bool tma_box_tile(int nx, int ny, int x0, int y0, int ty)
+{
+    return x0 + 32 <= nx && y0 + ty <= ny && nx >= kTmaBoxW && ny >= ty + 4;
+}
 // Shared-memory opt-in of the TMA kernels on the current device; call once
 // before the first launch_fused_tma, outside stream capture.
 cudaError_t prepare_fused_tma();
-// One time step of the FP32 lattices in one pass, one block per tile: every
-// full tile of a lattice that holds a whole box is staged by one TMA copy of
-// its population box and one of its reference-density box (the others load
-// as the plain one-pass kernel does).  A copy not complete after wait_cycles
-// SM clocks sets *err and ends the block; the copy of tile drop_tile (a test
-// hook, -1 for none) is never started.
+// One time step of the FP32 tiles [tile_offset, tile_offset + n_tiles) in
+// one pass, one block per tile, each tile staged by one TMA copy of its
+// population box and one of its reference-density box.  Every tile must be
+// full and of a lattice at least kTmaBoxW x (ty + 4) nodes (tma_box_tile);
+// the others go to Launch<float>::fused.  A copy not complete after
+// wait_cycles SM clocks sets *err = 1 and ends the block, a tile that is not
+// a box tile sets *err = 2; the copy of tile drop_tile (a test hook, -1 for
+// none) is never started.
 cudaError_t launch_fused_tma(const Lat<float> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
                              const TmaMaps *maps, int *err, long long wait_cycles, int drop_tile, int ty, cudaStream_t s);
 

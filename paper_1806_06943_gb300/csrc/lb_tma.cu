@@ -12,8 +12,10 @@
 // y0 - 2 .. y0 + TY + 1, all 18 population planes; a second box holds the 2
 // reference-density planes.  Parts of the box beyond the lattice are filled
 // with zeros by the copy and not used: the halo slots there (across a
-// periodic edge, or wall ghost rows) are formed as in fused_tile.  Ragged
-// tiles, and lattices narrower than the box, take the plain-load path.
+// periodic edge, or wall ghost rows) are formed as in fused_tile.  The
+// caller launches this kernel over the tiles that box_tile accepts and the
+// plain one-pass kernel over the others (ragged tiles, lattices smaller than
+// the box), so neither carries the other's registers.
 #include "lb_kernels.cuh"
 #include "lb_launch.h"
 
@@ -41,7 +43,7 @@ constexpr int kTmaMinBlocks = (225 * 1024) / (TmaBox<TYv>::kBytes + 8 * 1024) < 
 // the tile is full and its lattice holds a whole box (so its maps exist)
 __device__ __forceinline__ bool box_tile(const Lat<float> &G, int4 t, int tyv)
 {
-    return t.y + TX <= G.nx && t.z + tyv <= G.ny && G.nx >= kTmaBoxW && G.ny >= tyv + 2 * HALO;
+    return tma_box_tile(G.nx, G.ny, t.y, t.z, tyv);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -136,25 +138,31 @@ __device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ la
     const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
     const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
     const size_t c = (size_t)y * G.pitch + x;
+    // the node's own populations stay in the box: collide_site reads them there
+    const float *own = pop + cy * W + cx + 2;
     float fk[2][9], Rn[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
+        float v[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) fk[k][i] = pop[((k * 9 + i) * H + cy) * W + cx + 2];
+        for (int i = 0; i < 9; ++i) v[i] = own[(k * 9 + i) * H * W];
         Rn[k] = ref[(k * H + cy) * W + cx + 2];
-        const float r = Rn[k] + zeroth_moment<float>(fk[k]);
+        const float r = Rn[k] + zeroth_moment<float>(v);
         G.rho[parity ^ 1][(size_t)k * G.plane + c] = r;
         sm.srho[k][cy][cx] = r;
         sm.spsi[k][cy][cx] = psi_of<float>(r);
     }
     __syncthreads();
     const bool inner = t.y >= 1 && t.y + TX + 1 <= sm.L.nx && t.z >= 1 && t.z + TYv + 1 <= sm.L.ny;
-    if (inner) collide_site<float, true, SHv>(sm.L, G.f[parity ^ 1], sm.srho, sm.spsi, fk, Rn, x, y, cx, cy);
-    else collide_site<float, false, SHv>(sm.L, G.f[parity ^ 1], sm.srho, sm.spsi, fk, Rn, x, y, cx, cy);
+    if (inner)
+        collide_site<float, true, SHv, true>(sm.L, G.f[parity ^ 1], sm.srho, sm.spsi, fk, Rn, x, y, cx, cy, own, H * W);
+    else
+        collide_site<float, false, SHv, true>(sm.L, G.f[parity ^ 1], sm.srho, sm.spsi, fk, Rn, x, y, cx, cy, own, H * W);
 }
 
 // One block per tile: thread 0 starts the two copies, every thread waits
-// (bounded) on the mbarrier, then the tile is computed from the box.
+// (bounded) on the mbarrier, then the tile is computed from the box.  A tile
+// box_tile rejects is a caller error: it sets *err = 2 and is skipped.
 template <int TYv>
 __global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
     k_fused_tma(const Lat<float> *__restrict__ lats, const int4 *__restrict__ tiles, int tile_offset, int parity,
@@ -167,7 +175,7 @@ __global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
     __shared__ CollideSmem<float, TYv> sm;
     const int4 t = tiles[tile_offset + blockIdx.x];
     if (!box_tile(lats[t.x], t, TYv)) {
-        fused_tile<float, TYv, false>(lats, t, parity, sm);
+        if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(err, 2);
         return;
     }
     const int tid = threadIdx.y * TX + threadIdx.x;
