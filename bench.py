@@ -409,7 +409,7 @@ def main():
         # Laplace fit at ratio 1 after the run so far (not converged; sanity only)
         # FP64 on the same batch
         b64 = make_batch(lb, specs, fields, lb.LB_FP64, sptr)
-        b64.set_config(mode, 4)
+        b64.set_config(lb.LB_MODE_FUSED if mode == lb.LB_MODE_TMA else mode, 4)
         b64.profile(3, flush.data_ptr(), FLUSH_BYTES)
         k64 = max(10, args.steps // 4)
         ms64 = b64.profile(k64, flush.data_ptr(), FLUSH_BYTES)
@@ -455,6 +455,7 @@ def main():
         e2e_iters = 3
         be = lb.Batch([dict(nx=s["nx"], ny=s["ny"], tau=s["tau"]) for s in specs], precision=lb.LB_FP32,
                       stream=sptr, **C6)
+        be.set_config(mode, args.tile_height)
         for i in range(len(specs)):
             be.set_fields(i, pinned[i])
         be.step(S)
@@ -475,21 +476,26 @@ def main():
         del be
 
         # adjoint: gradient of mu_r for the 512 x 128 channel emulsion, 5000
-        # steps, checkpoints every 250 (FP64 forward, recomputation, adjoint)
+        # steps, checkpoints every 250: FP32 forward and recomputation with the
+        # FP64 adjoint (the calibration configuration), and the FP64 forward
         from paper_1806_06943_gb300 import workloads as W
         rho_c, _, _, phi_c = W.hex_emulsion(512, 128, 0.5, R=12.0, spread=2.0, gap=3.0, walls=True,
                                             seed=W.BASE_SEED + 3)
-        Lc = lb.Lattice(512, 128, tau=(1.0, 1.0), g=(1e-6, 0.0), walls=1, wall_mode=1, wall_rho=(0.03, 1.0),
-                        stream=sptr, **C6)
-        Lc.set_fields(rho_c)
-        t0 = time.perf_counter()
-        Jc, dJc = Lc.grad(5000, 250, lb.LB_OBJ_MU_R)
-        tg = time.perf_counter() - t0
-        out["adjoint_channel_512x128"] = {"steps": 5000, "ckpt_every": 250, "phi_achieved": phi_c, "mu_r": Jc,
-                                          "dmu_r_dtheta": [float(v) for v in dJc],
-                                          "theta": "G_AB, G1, G2, tau_A, tau_B", "seconds": tg,
-                                          "forward_equivalent_mlups": 512 * 128 * 5000 / tg / 1e6}
-        del Lc
+        adj = {"steps": 5000, "ckpt_every": 250, "phi_achieved": phi_c, "theta": "G_AB, G1, G2, tau_A, tau_B"}
+        for prec, name in ((lb.LB_FP32, "fp32_forward"), (lb.LB_FP64, "fp64_forward")):
+            Lc = lb.Lattice(512, 128, tau=(1.0, 1.0), g=(1e-6, 0.0), walls=1, wall_mode=1, wall_rho=(0.03, 1.0),
+                            precision=prec, stream=sptr, **C6)
+            Lc.set_config(lb.LB_MODE_TMA if prec == lb.LB_FP32 else lb.LB_MODE_FUSED, 8)
+            Lc.set_fields(rho_c)
+            t0 = time.perf_counter()
+            Jc, dJc = Lc.grad(5000, 250, lb.LB_OBJ_MU_R)
+            tg = time.perf_counter() - t0
+            adj[name] = {"mu_r": Jc, "dmu_r_dtheta": [float(v) for v in dJc], "seconds": tg,
+                         "forward_equivalent_mlups": 512 * 128 * 5000 / tg / 1e6}
+            del Lc
+        g32, g64 = adj["fp32_forward"]["dmu_r_dtheta"], adj["fp64_forward"]["dmu_r_dtheta"]
+        adj["fp32_vs_fp64_max_rel"] = max(abs(x / y - 1) for x, y in zip(g32, g64))
+        out["adjoint_channel_512x128"] = adj
 
         # CPU oracle on a bounded sample (rank 0 only)
         if rank == 0 and world == 1:

@@ -256,9 +256,13 @@ int lb_profile(lb_handle *h, int32_t nsteps, void *flush_buf, size_t flush_bytes
  * each segment is then recomputed from its checkpoint and stepped backwards.
  * On return the lattice holds the state after nsteps steps (as lb_step would
  * leave it), *J the observable there and dJ[5] its gradient; parameter
- * gradients are accumulated in FP64.  Needs an LB_FP64 lattice; LB_OBJ_DP
- * needs a probe.  Device memory: (nsteps/ckpt_every + ckpt_every + 3) copies of
- * the populations plus 22 planes, allocated for the call.  Synchronises. */
+ * gradients are accumulated in FP64.  An LB_FP32 lattice runs the forward
+ * sweep and the recomputation in FP32 (checkpoints hold offsets and reference
+ * densities) and hands the adjoint FP64 populations f = h + w R of each step;
+ * the adjoint populations and the gradients stay FP64.  LB_OBJ_DP needs a
+ * probe.  Device memory, allocated for the call: nsteps/ckpt_every + 1
+ * states of the lattice's precision, ckpt_every + 2 (FP32: + 3) FP64
+ * population copies, plus 22 FP64 planes.  Synchronises. */
 int lb_grad(lb_handle *h, int64_t nsteps, int32_t ckpt_every, int32_t objective, double *J, double dJ[5]);
 
 /* ---- many independent lattices advanced together ------------------------- */

@@ -642,11 +642,22 @@ struct lb_engine {
     // checkpoint every ckpt steps and recomputation of each segment.
     int grad(int64_t nsteps, int ckpt, int objective, double *J, double dJ[5])
     {
-        if (precision != LB_FP64) return fail(LB_EINVAL, "lb_grad needs an LB_FP64 lattice");
         if (nsteps < 1 || ckpt < 1) return fail(LB_EINVAL, "lb_grad needs nsteps >= 1 and ckpt_every >= 1");
         if (!J || !dJ) return fail(LB_EINVAL, "J and dJ must not be NULL");
+        const bool f32 = precision == LB_FP32;
         const lb_params &p = P[0];
-        lbk::Lat<double> L = L64[0];
+        // the FP64 descriptor the adjoint kernels read (FP32 forward: the same
+        // layout and parameters in FP64)
+        lbk::Lat<double> L;
+        if (!f32) {
+            L = L64[0];
+        } else {
+            fill_lat(L, p);
+            L.pitch = L32[0].pitch;
+            L.plane = L32[0].plane;
+            L.has_probe = L32[0].has_probe;
+            for (int c = 0; c < 3; ++c) L.probe[c] = L32[0].probe[c];
+        }
         if (objective == LB_OBJ_MU_R) {
             if (!p.walls || p.g[0] == 0.0) return fail(LB_EINVAL, "mu_r needs walls and a body force g_x");
         } else if (objective == LB_OBJ_DP) {
@@ -656,23 +667,28 @@ struct lb_engine {
         }
         int rc = begin();
         if (rc) return rc;
-        const size_t pop = pop_bytes(0), plane_b = plane(0) * sizeof(double);
+        // pop64: one FP64 state, the adjoint's unit; state: one state of the
+        // forward precision (FP32: offsets + reference densities)
+        const size_t plane_b = plane(0) * sizeof(double), pop64 = 18 * plane_b;
+        const size_t state = pop_bytes(0) + ref_bytes(0);
         const int64_t nseg = (nsteps + ckpt - 1) / ckpt;
         const int seg_len = (int)std::min<int64_t>(ckpt, nsteps);
         const int tiles_x = (p.nx + lbk::TX - 1) / lbk::TX, tiles_y = (p.ny + lbk::TY - 1) / lbk::TY;
         const int ntl = tiles_x * tiles_y;
         char *mem = nullptr;
-        const size_t bytes = (size_t)nseg * pop + (size_t)seg_len * pop + 3 * pop + lbk::kAdjSlotCount * plane_b +
-                             2 * plane_b + (size_t)ntl * 8 * sizeof(double) + 8 * sizeof(double);
+        const size_t bytes = (size_t)nseg * state + (size_t)seg_len * pop64 + 2 * pop64 + state + (f32 ? pop64 : 0) +
+                             lbk::kAdjSlotCount * plane_b + 2 * plane_b + (size_t)ntl * 8 * sizeof(double) +
+                             8 * sizeof(double);
         if (cudaMalloc((void **)&mem, bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(LB_ENOMEM, "lb_grad: no room for checkpoints and adjoint buffers");
         }
         char *q = mem;
         auto take = [&](size_t b) { char *r = q; q += b; return r; };
-        char *ckpts = take((size_t)nseg * pop), *seg = take((size_t)seg_len * pop);
-        double *lam[2] = {(double *)take(pop), (double *)take(pop)};
-        char *final_state = take(pop);
+        char *ckpts = take((size_t)nseg * state), *seg = take((size_t)seg_len * pop64);
+        double *lam[2] = {(double *)take(pop64), (double *)take(pop64)};
+        char *final_state = take(state);
+        double *fT64 = f32 ? (double *)take(pop64) : nullptr;
         double *abuf = (double *)take(lbk::kAdjSlotCount * plane_b), *rho = (double *)take(2 * plane_b);
         double *gpart = (double *)take((size_t)ntl * 8 * sizeof(double)), *gout = (double *)take(8 * sizeof(double));
         cudaError_t ce = cudaMemsetAsync(gpart, 0, (size_t)ntl * 8 * sizeof(double), stream);
@@ -681,9 +697,27 @@ struct lb_engine {
             cudaFree(mem);
             return code;
         };
+        // the engine's state of population copy par <-> a compact state buffer
+        auto save_state = [&](char *dst, int par) {
+            cudaError_t e = cudaMemcpyAsync(dst, fbuf(0, par), pop_bytes(0), cudaMemcpyDeviceToDevice, stream);
+            if (e == cudaSuccess && f32)
+                e = cudaMemcpyAsync(dst + pop_bytes(0), rbuf(0, par), ref_bytes(0), cudaMemcpyDeviceToDevice, stream);
+            return e;
+        };
+        auto load_state = [&](const char *src, int par) {
+            cudaError_t e = cudaMemcpyAsync(fbuf(0, par), src, pop_bytes(0), cudaMemcpyDeviceToDevice, stream);
+            if (e == cudaSuccess && f32)
+                e = cudaMemcpyAsync(rbuf(0, par), src + pop_bytes(0), ref_bytes(0), cudaMemcpyDeviceToDevice, stream);
+            return e;
+        };
+        // FP64 populations of the engine's population copy par
+        auto state_f64 = [&](int par, double *out) {
+            if (!f32) return cudaMemcpyAsync(out, fbuf(0, par), pop64, cudaMemcpyDeviceToDevice, stream);
+            return lbk::offset_to_f64(L32[0], (const float *)fbuf(0, par), (const float *)rbuf(0, par), out, stream);
+        };
         // forward sweep, keeping a checkpoint at the start of every segment
         for (int64_t s = 0; s < nseg && ce == cudaSuccess; ++s) {
-            ce = cudaMemcpyAsync(ckpts + s * pop, fbuf(0, parity), pop, cudaMemcpyDeviceToDevice, stream);
+            ce = save_state(ckpts + s * state, parity);
             if (ce == cudaSuccess && (rc = step(std::min<int64_t>(ckpt, nsteps - s * ckpt)))) return done(rc);
         }
         if (ce != cudaSuccess) return done(cuda_fail(ce, "lb_grad forward sweep"));
@@ -709,25 +743,27 @@ struct lb_engine {
             seed_a = 1.0 / nin;
             seed_b = -1.0 / nout;
         }
-        const int par_final = parity;
-        ce = cudaMemcpyAsync(final_state, fbuf(0, par_final), pop, cudaMemcpyDeviceToDevice, stream);
+        ce = save_state(final_state, parity);
         // seed: lam(T) = dJ/df(T)
-        const double *fT = (const double *)fbuf(0, par_final);
+        const double *fT = f32 ? fT64 : (const double *)fbuf(0, parity);
+        if (ce == cudaSuccess && f32) ce = state_f64(parity, fT64);
         if (ce == cudaSuccess) ce = lbk::adj_density(L, fT, rho, stream);
         if (ce == cudaSuccess) ce = lbk::adj_step(L, fT, rho, nullptr, abuf, gpart, lam[0], kind, seed_a, seed_b, stream);
         int cur = 0;
-        // backward over the segments, recomputing each from its checkpoint
+        // backward over the segments, recomputing each from its checkpoint in
+        // the forward precision; the adjoint steps read the FP64 populations
         for (int64_t s = nseg - 1; s >= 0 && ce == cudaSuccess; --s) {
             const int len = (int)std::min<int64_t>(ckpt, nsteps - s * ckpt);
-            ce = cudaMemcpyAsync(seg, ckpts + s * pop, pop, cudaMemcpyDeviceToDevice, stream);
+            ce = load_state(ckpts + s * state, 0);
+            if (ce == cudaSuccess) ce = state_f64(0, (double *)seg);
+            int par = 0;
             for (int j = 1; j < len && ce == cudaSuccess; ++j) {
-                ce = cudaMemcpyAsync(fbuf(0, 0), seg + (size_t)(j - 1) * pop, pop, cudaMemcpyDeviceToDevice, stream);
-                if (ce == cudaSuccess) ce = launch_step(0);
-                if (ce == cudaSuccess)
-                    ce = cudaMemcpyAsync(seg + (size_t)j * pop, fbuf(0, 1), pop, cudaMemcpyDeviceToDevice, stream);
+                ce = launch_step(par);
+                par ^= 1;
+                if (ce == cudaSuccess) ce = state_f64(par, (double *)(seg + (size_t)j * pop64));
             }
             for (int j = len - 1; j >= 0 && ce == cudaSuccess; --j) {
-                const double *ft = (const double *)(seg + (size_t)j * pop);
+                const double *ft = (const double *)(seg + (size_t)j * pop64);
                 ce = lbk::adj_density(L, ft, rho, stream);
                 if (ce == cudaSuccess)
                     ce = lbk::adj_step(L, ft, rho, lam[cur], abuf, gpart, lam[cur ^ 1], 0, 0.0, 0.0, stream);
@@ -738,11 +774,12 @@ struct lb_engine {
         double g[8] = {0};
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(g, gout, 8 * sizeof(double), cudaMemcpyDeviceToHost, stream);
         // put the final state back (the recomputation used both population copies)
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(fbuf(0, 0), final_state, pop, cudaMemcpyDeviceToDevice, stream);
+        if (ce == cudaSuccess) ce = load_state(final_state, 0);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
         if (ce != cudaSuccess) return done(cuda_fail(ce, "lb_grad adjoint sweep"));
         parity = 0;
         drop_graph();
+        if ((rc = check_timeout())) return done(rc);
         // theta = (G_AB, G1, G2, tau_A, tau_B); d omega / d tau = -omega^2
         dJ[0] = g[0];
         dJ[1] = g[1];
@@ -750,7 +787,6 @@ struct lb_engine {
         dJ[3] = -g[3] * L.omega[0] * L.omega[0];
         dJ[4] = -g[4] * L.omega[1] * L.omega[1];
         if (objective == LB_OBJ_MU_R) dJ[4] += -o.mu_r / (3.0 * ((p.tau[1] - 0.5) / 3.0));   // Q0(tau_B)
-        (void)par_final;
         return done(end());
     }
 

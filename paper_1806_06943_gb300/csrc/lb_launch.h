@@ -80,6 +80,9 @@ cudaError_t adj_density(const Lat<double> &L, const double *f, double *rho, cuda
 cudaError_t adj_step(const Lat<double> &L, const double *f, const double *rho, const double *lam_next, double *abuf,
                      double *gpart, double *lam_out, int seed_kind, double seed_a, double seed_b, cudaStream_t s);
 cudaError_t adj_reduce(const double *gpart, int n_tiles, double *out, cudaStream_t s);
+// FP64 populations f_i = h_i + w_i R of an FP32 state (18 offset planes h,
+// 2 reference-density planes R), pitched like the lattice (lb_fp32.cu).
+cudaError_t offset_to_f64(const Lat<float> &L, const float *h, const float *R, double *out, cudaStream_t s);
 constexpr int kAdjSlotCount = 20;
 
 // Record msg as the calling thread's lb_last_error() message.

@@ -5,7 +5,14 @@ through torch.autograd, and on the 512 x 128 channel emulsion over 5000 steps
 against finite differences of the FP64 GPU forward.  Tolerance: 1e-4
 relative per parameter of (G_AB, G1, G2, tau_A, tau_B), with an absolute
 floor of 1e-8 for the finite-difference truncation (h^2 times third
-derivatives of order one)."""
+derivatives of order one).
+
+The FP32 forward (offset populations, recomputed in FP32, converted to FP64
+populations for the FP64 adjoint) is held to the same 1e-4 against the FP64
+gradient and the FP64 finite differences: it differs from them by 2e-5 to
+4e-5.  Finite differences of the FP32 forward itself are no reference: its
+mu_r carries rounding of ~1e-6 relative, which h = 1e-4 turns into errors of
+~1e-2."""
 import numpy as np
 import pytest
 
@@ -102,7 +109,8 @@ def test_autograd_function(lbmod, oracle_mod):
 def test_channel_emulsion_512x128_5000_steps(lbmod):
     """Calibration workload: 512 x 128 channel, hexagonal emulsion near area
     fraction 0.5, 5000 steps, checkpoints every 250; central differences of
-    the FP64 GPU forward (each one bitwise equal to the oracle's arithmetic)."""
+    the FP64 GPU forward (each one bitwise equal to the oracle's arithmetic),
+    for the FP64 and the FP32 forward."""
     nx, ny = 512, 128
     rho, _, _, _ = W.hex_emulsion(nx, ny, 0.5, R=12.0, spread=2.0, gap=3.0, walls=True, seed=W.BASE_SEED + 3)
     kw = dict(g=(1e-6, 0.0), walls=1, wall_mode=1, wall_rho=(0.03, 1.0))
@@ -114,6 +122,13 @@ def test_channel_emulsion_512x128_5000_steps(lbmod):
         return L
 
     J, dJ = lat(theta).grad(5000, 250, lbmod.LB_OBJ_MU_R)
+    L32 = lbmod.Lattice(nx, ny, G_AB=theta[0], G1=theta[1], G2=theta[2], tau=(theta[3], theta[4]),
+                        precision=lbmod.LB_FP32, **kw)
+    L32.set_config(lbmod.LB_MODE_TMA, 8)
+    L32.set_fields(rho)
+    J32, dJ32 = L32.grad(5000, 250, lbmod.LB_OBJ_MU_R)      # FP32 forward, FP64 adjoint
+    assert abs(J32 - J) <= 1e-4 * abs(J)
+    assert close(dJ32, dJ), (dJ32, dJ)
     g = np.zeros(5)
     for a in range(5):
         tp, tm = theta.copy(), theta.copy()
@@ -124,11 +139,31 @@ def test_channel_emulsion_512x128_5000_steps(lbmod):
         Lm.step(5000)
         g[a] = (Lp.observables()["mu_r"] - Lm.observables()["mu_r"]) / 2e-4
     assert close(dJ, g), (dJ, g)
+    assert close(dJ32, g), (dJ32, g)
+
+
+def test_fp32_forward_gradient(lbmod):
+    """FP32 forward, FP64 adjoint: gradient within 1e-4 of the FP64 one, and
+    the lattice left where FP32 steps leave it."""
+    nx, ny, rho, kw = channel_case()
+    th = THETA0
+    res = {}
+    for prec in (lbmod.LB_FP64, lbmod.LB_FP32):
+        L = lbmod.Lattice(nx, ny, G_AB=th[0], G1=th[1], G2=th[2], tau=(th[3], th[4]), precision=prec, **kw)
+        L.set_fields(rho)
+        res[prec] = L.grad(120, 25, lbmod.LB_OBJ_MU_R)
+        M = lbmod.Lattice(nx, ny, G_AB=th[0], G1=th[1], G2=th[2], tau=(th[3], th[4]), precision=prec, **kw)
+        M.set_fields(rho)
+        M.step(120)
+        assert L.t == 120 and np.array_equal(L.get_populations(), M.get_populations())
+    (J32, g32), (J64, g64) = res[lbmod.LB_FP32], res[lbmod.LB_FP64]
+    assert abs(J32 - J64) <= 1e-5 * abs(J64)
+    assert close(g32, g64), (g32, g64)
 
 
 def test_rejects_unsupported(lbmod):
     L = lbmod.Lattice(16, 16, precision=lbmod.LB_FP32)
-    with pytest.raises(lbmod.LBError):
+    with pytest.raises(lbmod.LBError):   # no probe
         L.grad(10, 5, lbmod.LB_OBJ_DP)
     P = lbmod.Lattice(16, 16)
     with pytest.raises(lbmod.LBError):   # periodic: no mu_r
