@@ -96,9 +96,35 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// Staged slot (sx, sy) of the h-th position of the halo ring: two rows above,
+// two below, then the two columns on each side of the tile's rows.
+template <int TYv>
+__device__ __forceinline__ void ring_slot(int h, int &sx, int &sy)
+{
+    if (h < 2 * SW) {
+        sy = h / SW;
+        sx = h % SW;
+    } else if (h < 4 * SW) {
+        sy = TYv + HALO + (h - 2 * SW) / SW;
+        sx = (h - 2 * SW) % SW;
+    } else {
+        const int q = h - 4 * SW;
+        sy = HALO + q / 4;
+        sx = (q % 4 < 2) ? q % 4 : TX + q % 4;
+    }
+}
+
+// The slot's node lies beyond the lattice (across a periodic edge, or a wall
+// ghost row): not in the box's lattice part.
+__device__ __forceinline__ bool slot_outside(const Lat<float> &G, int4 t, int sx, int sy)
+{
+    const int gx = t.y + sx - HALO, gy = t.z + sy - HALO;
+    return gx < 0 || gx >= G.nx || gy < 0 || gy >= G.ny;
+}
+
 // fused_tile with the tile's and the halo's populations and reference
 // densities read from the box (pop: [18][H][40], ref: [2][H][40]).  The tile
-// is full.
+// is full.  Halo slots beyond the lattice were staged by the caller.
 template <int TYv>
 __device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ lats, int4 t, int parity,
                                                CollideSmem<float, TYv> &sm, const float *__restrict__ pop,
@@ -121,22 +147,8 @@ __device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ la
     constexpr int kRing = 4 * SW + 4 * TYv;
     for (int h = tid; h < kRing; h += TX * TYv) {
         int sx, sy;
-        if (h < 2 * SW) {
-            sy = h / SW;
-            sx = h % SW;
-        } else if (h < 4 * SW) {
-            sy = TYv + HALO + (h - 2 * SW) / SW;
-            sx = (h - 2 * SW) % SW;
-        } else {
-            const int q = h - 4 * SW;
-            sy = HALO + q / 4;
-            sx = (q % 4 < 2) ? q % 4 : TX + q % 4;
-        }
-        const int gx = t.y + sx - HALO, gy = t.z + sy - HALO;
-        if (gx < 0 || gx >= G.nx || gy < 0 || gy >= G.ny) {   // not in the box's lattice part
-            stage_slot<float, TYv, false>(G, t, parity, sm, sx, sy);
-            continue;
-        }
+        ring_slot<TYv>(h, sx, sy);
+        if (slot_outside(G, t, sx, sy)) continue;
         const float rA = slot_density(0, sx, sy), rB = slot_density(1, sx, sy);
         sm.srho[0][sy][sx] = rA;
         sm.srho[1][sy][sx] = rB;
@@ -204,6 +216,19 @@ __global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
             const int4 tn = tiles[tile_offset + blockIdx.x + ahead];
             tma_prefetch_3d(&maps[tn.x].pop[ti][parity], tn.y - 4, tn.z - HALO, 0);
             tma_prefetch_3d(&maps[tn.x].ref[ti][parity], tn.y - 4, tn.z - HALO, 0);
+        }
+    }
+    // halo slots beyond the lattice load their nodes directly (wrapped, or
+    // wall ghost rows): done while the copy is in flight
+    {
+        const Lat<float> &G = lats[t.x];
+        if (t.y == 0 || t.y + TX + HALO > G.nx || t.z < HALO || t.z + TYv + HALO > G.ny) {
+            constexpr int kRing = 4 * SW + 4 * TYv;
+            for (int h = tid; h < kRing; h += TX * TYv) {
+                int sx, sy;
+                ring_slot<TYv>(h, sx, sy);
+                if (slot_outside(G, t, sx, sy)) stage_slot<float, TYv, false>(G, t, parity, sm, sx, sy);
+            }
         }
     }
     __syncthreads();   // the barrier is initialised before anyone waits on it
