@@ -151,6 +151,26 @@ def droplet_array(L: int, n: int, R: float, seed: int) -> tuple[np.ndarray, floa
     return rho, phi
 
 
+def count_drops(rho_a: np.ndarray, threshold: float = 0.5) -> int:
+    """Connected regions (4-neighbour) of rho_A > threshold, periodic in x:
+    the number of drops, so that coalescence shows."""
+    from scipy import ndimage
+    lab, n = ndimage.label(rho_a > threshold)
+    parent = list(range(n + 1))
+
+    def find(i):
+        while parent[i] != i:
+            parent[i] = parent[parent[i]]
+            i = parent[i]
+        return i
+    for a, b in zip(lab[:, 0], lab[:, -1]):   # regions that continue across x = 0
+        if a and b:
+            ra, rb = find(a), find(b)
+            if ra != rb:
+                parent[ra] = rb
+    return len({find(i) for i in range(1, n + 1)})
+
+
 def rheology(cases: list[dict], L: int = 220, n: int = 5, steps: int = 200000, window: int = 40000,
              sample_every: int = 2000, precision: int = lb.LB_FP32, seed: int = W.BASE_SEED + 12,
              couplings=None) -> list[dict]:
@@ -158,7 +178,8 @@ def rheology(cases: list[dict], L: int = 220, n: int = 5, steps: int = 200000, w
     batch: L x L channel, fixed non-wetting wall densities, tau_B = 1.  The
     flow rate Q of every lattice is averaged over the last `window` steps;
     mu_r divides the Q of the droplet-free lattice of the same M and F_bar
-    (added where missing) by the case's."""
+    (added where missing) by the case's.  `drops` counts the drops at the
+    end (start: n * n), which shows whether they coalesced."""
     couplings = couplings or dict(G_AB=3.0, G1=-7.4, G2=6.4)
     keys = {(c["M"], c["F_bar"]) for c in cases}
     allc = list(cases) + [dict(R=0.0, M=m, F_bar=f) for (m, f) in sorted(keys)
@@ -184,11 +205,12 @@ def rheology(cases: list[dict], L: int = 220, n: int = 5, steps: int = 200000, w
             qs.append([o["Q"] for o in obs])
             fin &= np.array([o["finite"] == 1.0 for o in obs])
         q = np.mean(np.array(qs), axis=0)
+        drops = [count_drops(b.fields(i)["rho"][0]) if fin[i] and allc[i]["R"] > 0 else 0 for i in range(len(allc))]
         out = []
         for i, c in enumerate(allc):
             ref = next(j for j, d in enumerate(allc) if d["R"] == 0.0 and (d["M"], d["F_bar"]) == (c["M"], c["F_bar"]))
             ok = bool(fin[i] and fin[ref])
-            out.append(dict(R=c["R"], M=c["M"], F_bar=c["F_bar"], phi=phis[i], finite=ok,
+            out.append(dict(R=c["R"], M=c["M"], F_bar=c["F_bar"], phi=phis[i], finite=ok, drops=drops[i],
                             Q=float(q[i]) if fin[i] else float("nan"),
                             mu_r=float(q[ref] / q[i]) if ok else float("nan"),
                             Q_spread=float(np.ptp(np.array(qs)[:, i]) / q[i]) if fin[i] else float("nan")))
@@ -208,9 +230,14 @@ def demt_fit(phi, mu_r) -> tuple[float, float]:
 
 
 def eta_limits(M: float) -> tuple[float, float]:
-    """Intrinsic viscosity of undeformable drops (Taylor) and of freely
-    deformable ones (Douglas et al.) at viscosity ratio M = mu_B / mu_A, with
-    [eta]_inf = 2.5, as quoted in Sec. III D: returns (Douglas, Taylor)."""
-    taylor = (1.0 / M + ETA_INF) / (1.0 / M + 1.0)
-    douglas = (1.0 - 1.0 / M) / ((1.0 - 1.0 / M) / ETA_INF + 1.0 / M)
+    """Intrinsic viscosity of freely deformable drops (Douglas et al.) and of
+    undeformable ones (Taylor) at viscosity ratio M = mu_B / mu_A, with
+    [eta]_inf = 2.5, as quoted in Sec. III D: returns (Douglas, Taylor).
+    The printed formulas are read with their ratio as drop over matrix
+    viscosity, 1 / M here: so both give 2.5 for rigid drops (M -> 0) and
+    Taylor's gives 1 for bubbles, as Taylor's result does (at M = 1 either
+    reading gives 0 and 1.75)."""
+    lam = 1.0 / M
+    taylor = (1.0 / lam + ETA_INF) / (1.0 / lam + 1.0)
+    douglas = (1.0 - 1.0 / lam) / ((1.0 - 1.0 / lam) / ETA_INF + 1.0 / lam)
     return douglas, taylor

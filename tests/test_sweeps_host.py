@@ -1,0 +1,60 @@
+"""Host-side analysis of the physics sweeps, pinned to closed forms: the
+finite-difference interface width of the Fig. 2 caption on a tanh profile,
+the drop count (periodic in x), the fit of Eq. (20) and the two limits of
+the intrinsic viscosity quoted in Sec. III D."""
+import numpy as np
+import pytest
+
+from paper_1806_06943_gb300 import sweeps as S
+from paper_1806_06943_gb300 import workloads as W
+
+
+@pytest.mark.parametrize("w", [2.5, 4.0, 7.0])
+def test_width_of_tanh_profile(w):
+    # rho = mid + (d/2) tanh(2 (x - x0) / w), crossing halfway between nodes:
+    # the two nodes around it differ by d tanh(1 / w), so W = 1 / tanh(1 / w)
+    x = np.arange(200, dtype=np.float64)
+    lo, hi = 0.008, 1.041
+    prof = 0.5 * (hi + lo) + 0.5 * (hi - lo) * np.tanh(2.0 * (x - 99.5) / w)
+    assert S.interface_width(prof) == pytest.approx(1.0 / np.tanh(1.0 / w), rel=1e-9)
+    assert S.interface_width(prof) == pytest.approx(w, rel=0.02 + 1.0 / (3 * w * w))
+
+
+def test_width_of_a_drop_profile_counts_both_interfaces():
+    x = np.arange(300, dtype=np.float64)
+    prof = 0.5 + 0.5 * (np.tanh((x - 99.5) / 2.0) - np.tanh((x - 199.5) / 2.0))
+    assert S.interface_width(prof / prof.max()) == pytest.approx(1.0 / np.tanh(0.25), rel=1e-6)
+
+
+def test_count_drops_periodic_in_x():
+    rho = W.droplets(64, 40, [(10.0, 20.0), (40.0, 20.0)], [6.0, 6.0], seed=1, periodic=False)
+    assert S.count_drops(rho[0]) == 2
+    wrap = W.droplets(64, 40, [(0.5, 20.0)], [6.0], seed=1, periodic=False)   # split by x = 0
+    assert S.count_drops(wrap[0]) == 1
+    arr, phi = S.droplet_array(220, 5, 16.7, seed=3)
+    assert S.count_drops(arr[0]) == 25 and phi == pytest.approx(25 * np.pi * 16.7 ** 2 / 220 ** 2, rel=0.02)
+
+
+def test_demt_fit_recovers_eta():
+    phi = np.array([0.2, 0.3, 0.45, 0.6])
+    eta, r2 = S.demt_fit(phi, (1.0 - phi) ** -0.88)
+    assert eta == pytest.approx(0.88, rel=1e-12) and r2 == pytest.approx(1.0)
+
+
+def test_intrinsic_viscosity_limits():
+    assert S.eta_limits(1.0) == pytest.approx((0.0, 1.75))
+    d, t = S.eta_limits(1e-12)          # rigid drops (M = mu_B / mu_A -> 0): 2.5 in both
+    assert d == pytest.approx(2.5, rel=1e-9) and t == pytest.approx(2.5, rel=1e-9)
+    _, t = S.eta_limits(1e12)           # inviscid drops: Taylor's limit is 1
+    assert t == pytest.approx(1.0, rel=1e-9)
+    d, t = S.eta_limits(0.1)            # drops ten times more viscous than the matrix
+    assert 1.0 < d < t < 2.5
+
+
+def test_forcing_and_viscosity_ratio_readings():
+    # F_b = g rho_B^2 L^3 / (8 mu_B^2) with rho_B = 1, nu_B = 1/6: the
+    # Poiseuille centreline Reynolds number u_max L / nu_B
+    g = S.body_force(37.0, 220)
+    umax = g * 220 ** 2 / (8.0 / 6.0)
+    assert umax * 220 * 6.0 == pytest.approx(37.0, rel=1e-12)
+    assert S.tau_for_ratio(1.0) == 1.0 and S.tau_for_ratio(3.0) == pytest.approx(0.5 + 0.5 / 3.0)
