@@ -412,11 +412,21 @@ struct CollideSmem {
     Lat<real> L;   // descriptor copy: stores to the populations cannot alias it
 };
 
+// Moments of a node's FP32 offset populations that need no force: the first
+// moment per species, the density change rho - R moved into the offsets and
+// the offsets' residual sum dg after it (collide_site explains both).
+template <typename real>
+struct NodeMoments {
+    real j[2][2];
+    real delta[2];
+    real dg[2];
+};
+
 template <typename real, bool kInner, int SHv, bool kBox = false>
 __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW],
                                              const real (*spsi)[SHv][SW], real (&fk)[2][9], const real (&Rn)[2], int x,
                                              int y, int cx, int cy, const real *__restrict__ box = nullptr,
-                                             int box_plane = 0);
+                                             int box_plane = 0, const NodeMoments<real> *pre = nullptr);
 
 // Fused force + collision + push-streaming + bounce-back for one tile.  Every
 // thread of the block calls it and returns from it; it ends after the tile's
@@ -501,15 +511,37 @@ __global__ void __launch_bounds__(TX *TYv, kCollideMinBlocks<real, TYv>)
     collide_tile<real, TYv, false>(lats, tiles[tile_offset + blockIdx.x], parity, sm);
 }
 
+// The NodeMoments of a node whose populations are in a shared-memory box
+// (box[(k * 9 + i) * box_plane]), rho its density and Rn its reference: the
+// same operations, in the same order, as collide_site's own loop.
+template <typename real>
+__device__ __forceinline__ void node_moments(const real *__restrict__ box, int box_plane, const real (&rho)[2],
+                                             const real (&Rn)[2], NodeMoments<real> &nm)
+{
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        real f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = box[(k * 9 + i) * box_plane];
+        first_moment<real>(f, nm.j[k][0], nm.j[k][1]);
+        nm.delta[k] = rho[k] - Rn[k];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] -= (real)w9(i) * nm.delta[k];
+        nm.dg[k] = zeroth_moment<real>(f);
+    }
+}
+
 // Force, moments, u^eq, collision and push of the node (x, y), staged at
 // (cx, cy).  Its populations are fk (updated in place), or with kBox (FP32)
 // the shared-memory box: box[(k * 9 + i) * box_plane] is population i of
 // species k, read again where it is used with the same density offset
-// applied, which keeps 18 registers free; fk is then not used.
+// applied, which keeps 18 registers free; fk is then not used, and the
+// force-free moments come precomputed in *pre (node_moments).
 template <typename real, bool kInner, int SHv, bool kBox>
 __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW],
                                              const real (*spsi)[SHv][SW], real (&fk)[2][9], const real (&Rn)[2], int x,
-                                             int y, int cx, int cy, const real *__restrict__ box, int box_plane)
+                                             int y, int cx, int cy, const real *__restrict__ box, int box_plane,
+                                             const NodeMoments<real> *pre)
 {
     static_assert(!kBox || kOffset<real>, "the box form is FP32 only");
     real F[2][2], rho[2], m[2][2], dg[2] = {(real)0, (real)0}, delta[2] = {(real)0, (real)0};
@@ -517,12 +549,14 @@ __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restric
     for (int k = 0; k < 2; ++k) {
         force_at<real, SHv>(L, srho, spsi, k, cx, cy, F[k][0], F[k][1]);
         rho[k] = srho[k][cy][cx];
-        real fb[9];
         if constexpr (kBox) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) fb[i] = box[(k * 9 + i) * box_plane];
+            m[k][0] = pre->j[k][0] + (real)0.5 * F[k][0];   // Eq. (6), half force
+            m[k][1] = pre->j[k][1] + (real)0.5 * F[k][1];
+            delta[k] = pre->delta[k];
+            dg[k] = pre->dg[k];
+            continue;
         }
-        real(&f)[9] = kBox ? fb : fk[k];
+        real(&f)[9] = fk[k];
         real jx, jy;
         first_moment<real>(f, jx, jy);     // FP32: the reference density adds no momentum
         m[k][0] = jx + (real)0.5 * F[k][0];   // Eq. (6), half force

@@ -160,7 +160,7 @@ __device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ la
     const size_t c = (size_t)y * G.pitch + x;
     // the node's own populations stay in the box: collide_site reads them there
     const float *own = pop + cy * W + cx + 2;
-    float fk[2][9], Rn[2];
+    float fk[2][9], Rn[2], rn[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         float v[9];
@@ -171,13 +171,22 @@ __device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ la
         G.rho[parity ^ 1][(size_t)k * G.plane + c] = r;
         sm.srho[k][cy][cx] = r;
         sm.spsi[k][cy][cx] = psi_of<float>(r);
+        rn[k] = r;
     }
+    // the node's force-free moments: threads without a halo slot form them
+    // before the barrier (while the others stage the halo), the others after
+    NodeMoments<float> nm;
+    const bool early = tid >= kRing;
+    if (early) node_moments<float>(own, H * W, rn, Rn, nm);
     __syncthreads();
+    if (!early) node_moments<float>(own, H * W, rn, Rn, nm);
     const bool inner = t.y >= 1 && t.y + TX + 1 <= sm.L.nx && t.z >= 1 && t.z + TYv + 1 <= sm.L.ny;
     if (inner)
-        collide_site<float, true, SHv, true>(sm.L, G.f[parity ^ 1], sm.srho, sm.spsi, fk, Rn, x, y, cx, cy, own, H * W);
+        collide_site<float, true, SHv, true>(sm.L, G.f[parity ^ 1], sm.srho, sm.spsi, fk, Rn, x, y, cx, cy, own, H * W,
+                                             &nm);
     else
-        collide_site<float, false, SHv, true>(sm.L, G.f[parity ^ 1], sm.srho, sm.spsi, fk, Rn, x, y, cx, cy, own, H * W);
+        collide_site<float, false, SHv, true>(sm.L, G.f[parity ^ 1], sm.srho, sm.spsi, fk, Rn, x, y, cx, cy, own,
+                                              H * W, &nm);
 }
 
 // One block per tile: thread 0 starts the two copies, every thread waits
