@@ -70,15 +70,17 @@ extern "C" {
  *   densities of its tile and 2-node halo from the populations itself (no
  *   separate density pass), then runs the fused force / collision / push;
  *   replayed 32 steps per CUDA graph.
- * LB_MODE_TMA (LB_FP32 only): LB_MODE_FUSED with every tile whose box (the
- *   tile, 4 columns each side, 2 rows above and below) lies inside its
- *   lattice brought into shared memory by one tensor-memory-accelerator copy
- *   of its 18 population planes and one of its 2 reference-density planes,
- *   completed on an mbarrier; blocks stay resident and walk the tiles, the
- *   next box in flight while the current tile computes.  Other tiles load as
- *   in LB_MODE_FUSED.  Same arithmetic as LB_MODE_FUSED.  A copy not complete
- *   within the wait limit (default 2 s) ends the block and the next
- *   synchronising call returns LB_ETIMEOUT. */
+ * LB_MODE_TMA (LB_FP32 only): LB_MODE_FUSED with every full tile of a
+ *   lattice of at least 40 x (tile height + 4) nodes brought into shared
+ *   memory by tensor-memory-accelerator copies of its box (the tile, 4
+ *   columns each side, 2 rows above and below; 18 population planes and 2
+ *   reference-density planes), completed on an mbarrier; each block also
+ *   prefetches into L2 the box of a tile about a wave of blocks later.  Halo
+ *   nodes across a periodic edge or on wall ghost rows, ragged tiles and
+ *   smaller lattices load as in LB_MODE_FUSED.  Same arithmetic as
+ *   LB_MODE_FUSED, same results.  A copy not complete within the wait limit
+ *   (default 2 s) ends its block and the next synchronising call returns
+ *   LB_ETIMEOUT. */
 #define LB_MODE_LAUNCH 0
 #define LB_MODE_PERSISTENT 1
 #define LB_MODE_FUSED 2
