@@ -29,10 +29,15 @@ def lbmod():
     return lb
 
 
+def bench_mode(lbmod, precision):
+    """The benchmark's configuration: FP32 staged by TMA, FP64 one-pass."""
+    return lbmod.LB_MODE_TMA if precision == lbmod.LB_FP32 else lbmod.LB_MODE_FUSED
+
+
 def sweep(lbmod, precision, steps):
     specs = W.laplace_sweep_specs()
     b = lbmod.Batch([dict(nx=s["nx"], ny=s["ny"], tau=s["tau"]) for s in specs], precision=precision, **C6)
-    b.set_config(lbmod.LB_MODE_FUSED, 8)
+    b.set_config(bench_mode(lbmod, precision), 8)
     for i, s in enumerate(specs):
         b.set_fields(i, W.droplet(s["nx"], s["ny"], s["R"], seed=W.BASE_SEED + 1 + i))
         b.set_probe(i, s["nx"] / 2, s["ny"] / 2, s["R"])
@@ -85,7 +90,7 @@ def channel_field(phi):
 def run_series(lbmod, precision, specs, fields):
     """mu_r of every lattice at every checkpoint, all lattices in one batch."""
     b = lbmod.Batch(specs, precision=precision, **C6)
-    b.set_config(lbmod.LB_MODE_FUSED, 8)
+    b.set_config(bench_mode(lbmod, precision), 8)
     for i, r in enumerate(fields):
         b.set_fields(i, r)
     out, t = [], 0
@@ -148,7 +153,7 @@ def test_single_phase_channel_fp32_vs_fp64_50k_steps(lbmod):
     for prec in (lbmod.LB_FP32, lbmod.LB_FP64):
         L = lbmod.Lattice(NX, NY, tau=(2.0, 1.0), g=(1e-6, 0.0), walls=1, wall_mode=1, wall_rho=(0.03, 1.0),
                           precision=prec, **C6)
-        L.set_config(lbmod.LB_MODE_FUSED, 8)
+        L.set_config(bench_mode(lbmod, prec), 8)
         L.set_fields(rho)
         L.step(50000)
         mu[prec] = L.observables()["mu_r"]

@@ -1,5 +1,6 @@
 """Parity at the benchmark's full sizes, in the launch configuration the
-benchmark times (one-pass step, tiles of 32 x 8, FP32 and FP64): sampled
+benchmark times (tiles of 32 x 8; FP32 one-pass step staged by TMA, FP64
+one-pass step): sampled
 nodes against the oracle, which advances a 21 x 21 patch of the initial field
 around each sampled node.  After two steps a node depends only on nodes
 within 6 lattice units, and its diagnostics (forces included) on nodes within
@@ -28,6 +29,10 @@ def lbmod():
     build.build()
     from paper_1806_06943_gb300 import lb
     return lb
+
+
+def bench_mode(lbmod, precision):
+    return lbmod.LB_MODE_TMA if precision == lbmod.LB_FP32 else lbmod.LB_MODE_FUSED
 
 
 def patch(field, cx, cy):
@@ -62,7 +67,7 @@ def test_dense_emulsion_4096_sampled(lbmod, oracle_mod, emulsion4096, precision,
     rho0 = emulsion4096
     tau = (3.0, 1.0)
     L = lbmod.Lattice(n, n, tau=tau, precision=precision, **C6)
-    L.set_config(lbmod.LB_MODE_FUSED, 8)
+    L.set_config(bench_mode(lbmod, precision), 8)
     L.set_fields(rho0)
     L.step(2)
     f = L.fields()
@@ -78,7 +83,7 @@ def test_laplace_sweep_24_sampled(lbmod, oracle_mod, precision, tol_rho, tol_u):
     specs = W.laplace_sweep_specs()
     fields0 = [W.droplet(s["nx"], s["ny"], s["R"], seed=W.BASE_SEED + 1 + i) for i, s in enumerate(specs)]
     b = lbmod.Batch([dict(nx=s["nx"], ny=s["ny"], tau=s["tau"]) for s in specs], precision=precision, **C6)
-    b.set_config(lbmod.LB_MODE_FUSED, 8)
+    b.set_config(bench_mode(lbmod, precision), 8)
     for i, r in enumerate(fields0):
         b.set_fields(i, r)
     b.step(2)
@@ -97,7 +102,7 @@ def test_mass_conserved_at_full_size(lbmod, emulsion4096, precision, tol):
     n = 4096
     rho0 = emulsion4096
     L = lbmod.Lattice(n, n, tau=(3.0, 1.0), precision=precision, **C6)
-    L.set_config(lbmod.LB_MODE_FUSED, 8)
+    L.set_config(bench_mode(lbmod, precision), 8)
     L.set_fields(rho0)
     o0 = L.observables()
     L.step(100)
