@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
 
 // Distance, in quarters of a wave of resident blocks, between a tile and the
 // tile whose boxes it prefetches into L2 (0: none).  Half a wave to a wave
-// measured alike (0.581-0.583 ms per 4096^2 step against 0.597 without);
+// measured alike (a 4096^2 step 3 % shorter than without the prefetch);
 // beyond it the boxes are prefetched too early.
 constexpr int kPrefetchQuarterWaves = 3;
 
