@@ -1,0 +1,44 @@
+"""The benchmark's output contract on the CPU: the reference arm (the CPU
+oracle) prints one JSON line with every key the benchmark line carries, and
+the DRAM traffic of a step kernel is reported only for the kernel, workload
+and kernel sources it was captured on."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+        "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"}
+
+
+def test_reference_arm_prints_one_json_line(oracle_mod):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1"], capture_output=True, text=True, cwd=ROOT, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    assert KEYS <= set(out), KEYS - set(out)
+    assert out["impl"] == "reference" and out["metric"] == "2-species MLUPS" and out["unit"] == "MLUPS"
+    assert out["value"] > 0 and out["higher_is_better"] is True and out["steps"] == 2 and out["warmup"] == 1
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] == 1
+    assert out["cpu_baseline"]["value"] == out["value"]
+    assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["value"] == out["value"]
+    assert out["config"]["workload"] == "laplace_sweep_24"
+
+
+def test_traffic_is_keyed_by_kernel_workload_and_sources():
+    import bench
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        entries = json.load(f)
+    e = entries[0]
+    got = bench.kernel_traffic(e["workload"], e["kernel"])
+    if e["kernel_source_sha1"] == bench.kernel_source_sha1():
+        assert got == float(e["bytes_per_launch"])
+    else:
+        assert got is None
+    assert bench.kernel_traffic("dense_emulsion_4096", e["kernel"]) is None
+    assert bench.kernel_traffic(e["workload"], "k_collide<float, 4>") is None
