@@ -77,6 +77,28 @@ def droplet(nx, ny, R, cx=None, cy=None, seed=BASE_SEED, noise=NOISE, hi=MAJORIT
     return _fill(disk_mask(nx, ny, cx, cy, R, periodic), seed, hi, lo, noise)
 
 
+def smooth_droplet(nx, ny, R, width, cx=None, cy=None, seed=BASE_SEED, noise=NOISE, hi=MAJORITY,
+                   lo=MINORITY) -> np.ndarray:
+    """One species-A disk of radius R in species B with a tanh interface of
+    the given width (rho_A = lo + (hi - lo) (1 - tanh(2 (r - R) / width)) / 2,
+    rho_B its mirror), periodic (minimum image)."""
+    cx = nx / 2 if cx is None else cx
+    cy = ny / 2 if cy is None else cy
+    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    dx = np.abs(x - cx)
+    dx = np.minimum(dx, nx - dx)
+    dy = np.abs(y - cy)
+    dy = np.minimum(dy, ny - dy)
+    a = 0.5 * (1.0 - np.tanh(2.0 * (np.sqrt(dx * dx + dy * dy) - R) / width))
+    rho = np.empty((2, ny, nx))
+    rho[0] = lo + (hi - lo) * a
+    rho[1] = hi + lo - rho[0]
+    if noise:
+        rho[0] += uniform_noise(seed, 0, nx, ny, noise)
+        rho[1] += uniform_noise(seed, 1, nx, ny, noise)
+    return rho
+
+
 def droplets(nx, ny, centres, radii, seed=BASE_SEED, noise=NOISE, hi=MAJORITY, lo=MINORITY,
              periodic=True) -> np.ndarray:
     """Several species-A disks (rasterised per bounding box) in species B."""
