@@ -58,3 +58,18 @@ def test_forcing_and_viscosity_ratio_readings():
     umax = g * 220 ** 2 / (8.0 / 6.0)
     assert umax * 220 * 6.0 == pytest.approx(37.0, rel=1e-12)
     assert S.tau_for_ratio(1.0) == 1.0 and S.tau_for_ratio(3.0) == pytest.approx(0.5 + 0.5 / 3.0)
+
+
+def test_smooth_droplet_profile():
+    n, R, w = 128, 30.0, 4.0
+    rho = W.smooth_droplet(n, n, R, w, noise=0.0)
+    lo, hi = W.MINORITY, W.MAJORITY
+    assert np.allclose(rho[0] + rho[1], hi + lo)
+    assert rho[0][64, 64] == pytest.approx(hi, abs=1e-12) and rho[0][0, 0] == pytest.approx(lo, abs=1e-12)
+    r = np.abs(np.arange(n) - 64.0)
+    prof = rho[0][64]
+    # the mean density is crossed at r = R, here on a node: the width
+    # definition of the Fig. 2 caption then differences that node and the
+    # next, rho(R) - rho(R + 1) = (hi - lo) tanh(2 / w) / 2
+    assert np.interp(R, r[64:], prof[64:]) == pytest.approx(0.5 * (hi + lo), abs=1e-12)
+    assert S.interface_width(prof) == pytest.approx(2.0 / np.tanh(2.0 / w), rel=1e-9)
