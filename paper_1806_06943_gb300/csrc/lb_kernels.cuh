@@ -215,6 +215,26 @@ __device__ __forceinline__ void force_at(const Lat<real> &L, const real (*srho)[
     Fy = -G1 * psi * s1y - G2 * psi * s2y - GAB * rho * s3y + rho * L.g[1];
 }
 
+// The staged density and psi tiles of the species as one [row][col] plane
+// per species and field, as collide_site reads them: species k's density
+// and force at a staged node, and rho_k(x) - rho_k(x + e), the difference a
+// push re-references with.  collide_site asks for species 0, then 1.
+template <typename real, int SHv>
+struct SplitStage {
+    const real (*srho)[SHv][SW];
+    const real (*spsi)[SHv][SW];
+    __device__ __forceinline__ real density(int k, int cy, int cx) const { return srho[k][cy][cx]; }
+    __device__ __forceinline__ void force(const Lat<real> &L, int k, int cx, int cy, real &Fx, real &Fy) const
+    {
+        force_at<real, SHv>(L, srho, spsi, k, cx, cy, Fx, Fy);
+    }
+    template <int EX, int EY>
+    __device__ __forceinline__ real density_step(int k, int cx, int cy) const
+    {
+        return srho[k][cy][cx] - srho[k][cy + EY][cx + EX];
+    }
+};
+
 // e_i . u in the order e_x u_x + e_y u_y, zero products dropped.
 template <typename real, int EX, int EY>
 __device__ __forceinline__ real edot(real ux, real uy)
@@ -257,15 +277,15 @@ __device__ __forceinline__ real collide_dir(real f, real rho, real ux, real uy, 
 // Store the post-collision value of direction I of species k at x + e_i
 // (half-way bounce-back: back to x, reversed).  FP32: re-reference the offset
 // from rho(x) to rho(x + e_i), the reference the next step reads there.
-template <typename real, int I, bool kInner, int SHv>
-__device__ __forceinline__ void push_dir(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW], int k,
-                                         int x, int y, int cx, int cy, real v)
+template <typename real, int I, bool kInner, class Stage>
+__device__ __forceinline__ void push_dir(const Lat<real> &L, real *__restrict__ fn, const Stage &sg, int k, int x,
+                                         int y, int cx, int cy, real v)
 {
     constexpr int EX = ex9(I), EY = ey9(I);
     if constexpr (kOffset<real> && I != 0) {
         // the next step's reference at the destination is its density now
         if (kInner || !(EY != 0 && L.walls && (y + EY < 0 || y + EY >= L.ny)))
-            v += (real)w9(I) * (srho[k][cy][cx] - srho[k][cy + EY][cx + EX]);
+            v += (real)w9(I) * sg.template density_step<EX, EY>(k, cx, cy);
     }
     if constexpr (kInner) {
         // node and destination inside the lattice: a constant offset
@@ -303,9 +323,9 @@ struct SpeciesTerms {
 };
 
 // Collision and push of direction I of both species, fI[k] the node's
-// population (FP32: its offset) of that direction.
-template <typename real, int I, bool kInner, int SHv>
-__device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW],
+// population (FP32: its offset) of that direction; sg the staged densities.
+template <typename real, int I, bool kInner, class Stage>
+__device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__restrict__ fn, const Stage &sg,
                                                  const real (&fI)[2], const real (&rho)[2], real ux, real uy, real uu,
                                                  const real (&F)[2][2], const SpeciesTerms<real> &st, int x, int y,
                                                  int cx, int cy)
@@ -316,7 +336,7 @@ __device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__res
         for (int k = 0; k < 2; ++k) {
             const real v = collide_dir<real, I>(fI[k], rho[k], ux, uy, uu, F[k][0], F[k][1], L.omega[k],
                                                 L.aw[k][cls9(I)]);
-            push_dir<real, I, kInner, SHv>(L, fn, srho, k, x, y, cx, cy, v);
+            push_dir<real, I, kInner>(L, fn, sg, k, x, y, cx, cy, v);
         }
     } else {
         // Eq. (2) less w rho (the node's own density is the offset), and Eq. (5)
@@ -335,7 +355,7 @@ __device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__res
             const real geq = st.wr[k][C] * q + (real)w9(I) * st.dg[k];
             const real f = fI[k];
             const real v = (f + L.omega[k] * (geq - f)) + Cg;
-            push_dir<real, I, kInner, SHv>(L, fn, srho, k, x, y, cx, cy, v);
+            push_dir<real, I, kInner>(L, fn, sg, k, x, y, cx, cy, v);
         }
     }
 }
@@ -422,11 +442,11 @@ struct NodeMoments {
     real dg[2];
 };
 
-template <typename real, bool kInner, int SHv, bool kBox = false>
-__device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW],
-                                             const real (*spsi)[SHv][SW], real (&fk)[2][9], const real (&Rn)[2], int x,
-                                             int y, int cx, int cy, const real *__restrict__ box = nullptr,
-                                             int box_plane = 0, const NodeMoments<real> *pre = nullptr);
+template <typename real, bool kInner, bool kBox = false, class Stage>
+__device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const Stage &sg,
+                                             real (&fk)[2][9], const real (&Rn)[2], int x, int y, int cx, int cy,
+                                             const real *__restrict__ box = nullptr, int box_plane = 0,
+                                             const NodeMoments<real> *pre = nullptr);
 
 // Fused force + collision + push-streaming + bounce-back for one tile.  Every
 // thread of the block calls it and returns from it; it ends after the tile's
@@ -499,8 +519,9 @@ __device__ __forceinline__ void collide_tile(const Lat<real> *__restrict__ lats,
     }
     // tiles whose pushes stay inside the lattice (no wrap, no wall) take constant offsets
     const bool inner = t.y >= 1 && t.y + TX + 1 <= sm.L.nx && t.z >= 1 && t.z + TYv + 1 <= sm.L.ny;
-    if (inner) collide_site<real, true, TYv + 2 * HALO>(sm.L, fn, sm.srho, sm.spsi, fk, Rn, x, y, cx, cy);
-    else collide_site<real, false, TYv + 2 * HALO>(sm.L, fn, sm.srho, sm.spsi, fk, Rn, x, y, cx, cy);
+    const SplitStage<real, TYv + 2 * HALO> sg{sm.srho, sm.spsi};
+    if (inner) collide_site<real, true>(sm.L, fn, sg, fk, Rn, x, y, cx, cy);
+    else collide_site<real, false>(sm.L, fn, sg, fk, Rn, x, y, cx, cy);
 }
 
 template <typename real, int TYv>
@@ -537,18 +558,17 @@ __device__ __forceinline__ void node_moments(const real *__restrict__ box, int b
 // species k, read again where it is used with the same density offset
 // applied, which keeps 18 registers free; fk is then not used, and the
 // force-free moments come precomputed in *pre (node_moments).
-template <typename real, bool kInner, int SHv, bool kBox>
-__device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const real (*srho)[SHv][SW],
-                                             const real (*spsi)[SHv][SW], real (&fk)[2][9], const real (&Rn)[2], int x,
-                                             int y, int cx, int cy, const real *__restrict__ box, int box_plane,
-                                             const NodeMoments<real> *pre)
+template <typename real, bool kInner, bool kBox, class Stage>
+__device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const Stage &sg,
+                                             real (&fk)[2][9], const real (&Rn)[2], int x, int y, int cx, int cy,
+                                             const real *__restrict__ box, int box_plane, const NodeMoments<real> *pre)
 {
     static_assert(!kBox || kOffset<real>, "the box form is FP32 only");
     real F[2][2], rho[2], m[2][2], dg[2] = {(real)0, (real)0}, delta[2] = {(real)0, (real)0};
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        force_at<real, SHv>(L, srho, spsi, k, cx, cy, F[k][0], F[k][1]);
-        rho[k] = srho[k][cy][cx];
+        sg.force(L, k, cx, cy, F[k][0], F[k][1]);
+        rho[k] = sg.density(k, cy, cx);
         if constexpr (kBox) {
             m[k][0] = pre->j[k][0] + (real)0.5 * F[k][0];   // Eq. (6), half force
             m[k][1] = pre->j[k][1] + (real)0.5 * F[k][1];
@@ -608,23 +628,23 @@ __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restric
     };
     real fI[2];
     dir_pops(0, fI);
-    collide_push_dir<real, 0, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 0, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
     dir_pops(1, fI);
-    collide_push_dir<real, 1, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 1, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
     dir_pops(2, fI);
-    collide_push_dir<real, 2, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 2, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
     dir_pops(3, fI);
-    collide_push_dir<real, 3, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 3, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
     dir_pops(4, fI);
-    collide_push_dir<real, 4, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 4, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
     dir_pops(5, fI);
-    collide_push_dir<real, 5, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 5, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
     dir_pops(6, fI);
-    collide_push_dir<real, 6, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 6, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
     dir_pops(7, fI);
-    collide_push_dir<real, 7, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 7, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
     dir_pops(8, fI);
-    collide_push_dir<real, 8, kInner, SHv>(L, fn, srho, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
+    collide_push_dir<real, 8, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
 }
 
 // ---- one-pass step ------------------------------------------------------------
@@ -644,37 +664,41 @@ __device__ __forceinline__ real node_density(const Lat<real> &L, int k, int gx, 
     return r;
 }
 
-// Densities and psi of staged slot (sx, sy) of tile t (slot (HALO, HALO) is
-// the tile's first node) from the populations of its node: x wraps; beyond
-// the lattice in y, periodic wrap, or a wall ghost row (the mirrored fluid
-// row, or the fixed wall densities).
-template <typename real, int TYv, bool kCG>
-__device__ __forceinline__ void stage_slot(const Lat<real> &G, int4 t, int parity, CollideSmem<real, TYv> &sm, int sx,
-                                           int sy)
+// Densities of staged slot (sx, sy) of tile t (slot (HALO, HALO) is the
+// tile's first node) from the populations of its node: x wraps; beyond the
+// lattice in y, periodic wrap, or a wall ghost row (the mirrored fluid row,
+// or the fixed wall densities).
+template <typename real, bool kCG>
+__device__ __forceinline__ void slot_densities(const Lat<real> &G, int4 t, int parity, int sx, int sy, real &rA,
+                                               real &rB)
 {
     const int nx = G.nx, ny = G.ny;
     const int gx = wrap_index(t.y + sx - HALO, nx);
     int gy = t.z + sy - HALO;
-    real rA, rB;
-    bool fixed = false;
     if (gy < 0 || gy >= ny) {
         if (G.walls) {
             if (G.wall_mode == 1) {
                 rA = G.wall_rho[0];
                 rB = G.wall_rho[1];
-                fixed = true;
-            } else {
-                gy = gy < 0 ? -1 - gy : 2 * ny - 1 - gy;
-                gy = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);  // rows no valid node reads
+                return;
             }
+            gy = gy < 0 ? -1 - gy : 2 * ny - 1 - gy;
+            gy = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);  // rows no valid node reads
         } else {
             gy = wrap_index(gy, ny);
         }
     }
-    if (!fixed) {
-        rA = node_density<real, kCG>(G, 0, gx, gy, parity);
-        rB = node_density<real, kCG>(G, 1, gx, gy, parity);
-    }
+    rA = node_density<real, kCG>(G, 0, gx, gy, parity);
+    rB = node_density<real, kCG>(G, 1, gx, gy, parity);
+}
+
+// The same, staged with psi into the tile's density and psi planes.
+template <typename real, int TYv, bool kCG>
+__device__ __forceinline__ void stage_slot(const Lat<real> &G, int4 t, int parity, CollideSmem<real, TYv> &sm, int sx,
+                                           int sy)
+{
+    real rA, rB;
+    slot_densities<real, kCG>(G, t, parity, sx, sy, rA, rB);
     sm.srho[0][sy][sx] = rA;
     sm.srho[1][sy][sx] = rB;
     sm.spsi[0][sy][sx] = psi_of<real>(rA);
@@ -752,8 +776,9 @@ __device__ __forceinline__ void fused_tile(const Lat<real> *__restrict__ lats, i
     __syncthreads();
     if (!valid) return;
     const bool inner = t.y >= 1 && t.y + TX + 1 <= sm.L.nx && t.z >= 1 && t.z + TYv + 1 <= sm.L.ny;
-    if (inner) collide_site<real, true, SHv>(sm.L, fn, sm.srho, sm.spsi, fk, Rn, x, y, cx, cy);
-    else collide_site<real, false, SHv>(sm.L, fn, sm.srho, sm.spsi, fk, Rn, x, y, cx, cy);
+    const SplitStage<real, SHv> sg{sm.srho, sm.spsi};
+    if (inner) collide_site<real, true>(sm.L, fn, sg, fk, Rn, x, y, cx, cy);
+    else collide_site<real, false>(sm.L, fn, sg, fk, Rn, x, y, cx, cy);
 }
 
 template <typename real, int TYv>

@@ -96,6 +96,114 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// Staged density and psi of the tile and its halo as (species A, species B)
+// pairs per node, so that one 64-bit shared load serves both species.
+template <int TYv>
+struct PairSmem {
+    float2 sr[TYv + 2 * HALO][SW];
+    float2 sp[TYv + 2 * HALO][SW];
+    Lat<float> L;   // descriptor copy: stores to the populations cannot alias it
+};
+
+// q9_sum (FP32) of both components of a pair plane: the same differences of
+// opposite neighbours and the same expressions, per species.
+template <int SHv>
+__device__ __forceinline__ void q9_pair(const float2 (*s)[SW], int cx, int cy, float (&sx)[2], float (&sy)[2])
+{
+    const float W1 = (float)(1.0 / 9.0), W2 = (float)(1.0 / 36.0);
+    const float2 e = s[cy][cx + 1], w = s[cy][cx - 1], n = s[cy + 1][cx], so = s[cy - 1][cx];
+    const float2 ne = s[cy + 1][cx + 1], sw = s[cy - 1][cx - 1], se = s[cy - 1][cx + 1], nw = s[cy + 1][cx - 1];
+    {
+        const float dE = e.x - w.x, dN = n.x - so.x, d1 = ne.x - sw.x, d2 = se.x - nw.x;
+        sx[0] = W1 * dE + W2 * (d1 + d2);
+        sy[0] = W1 * dN + W2 * (d1 - d2);
+    }
+    {
+        const float dE = e.y - w.y, dN = n.y - so.y, d1 = ne.y - sw.y, d2 = se.y - nw.y;
+        sx[1] = W1 * dE + W2 * (d1 + d2);
+        sy[1] = W1 * dN + W2 * (d1 - d2);
+    }
+}
+
+// q25_sum (FP32) of both components of a pair plane, same classes and order.
+template <int SHv>
+__device__ __forceinline__ void q25_pair(const float2 (*s)[SW], int cx, int cy, float (&sx)[2], float (&sy)[2])
+{
+    float ax[2] = {0.f, 0.f}, ay[2] = {0.f, 0.f};
+#pragma unroll
+    for (int a = 1; a <= 2; ++a) {   // axis classes (a,0) and (0,a)
+        const float p = (float)(p25(a * a) * a);
+        const float2 xp = s[cy][cx + a], xm = s[cy][cx - a], yp = s[cy + a][cx], ym = s[cy - a][cx];
+        ax[0] += p * (xp.x - xm.x);
+        ay[0] += p * (yp.x - ym.x);
+        ax[1] += p * (xp.y - xm.y);
+        ay[1] += p * (yp.y - ym.y);
+    }
+#pragma unroll
+    for (int a = 1; a <= 2; ++a)
+#pragma unroll
+        for (int b = 1; b <= 2; ++b) {   // off-axis classes (a,b)
+            const float2 pp = s[cy + b][cx + a], mm = s[cy - b][cx - a], pm = s[cy - b][cx + a], mp = s[cy + b][cx - a];
+            const float p = (float)p25(a * a + b * b);
+            {
+                const float d1 = pp.x - mm.x, d2 = pm.x - mp.x;
+                ax[0] += (p * (float)a) * (d1 + d2);
+                ay[0] += (p * (float)b) * (d1 - d2);
+            }
+            {
+                const float d1 = pp.y - mm.y, d2 = pm.y - mp.y;
+                ax[1] += (p * (float)a) * (d1 + d2);
+                ay[1] += (p * (float)b) * (d1 - d2);
+            }
+        }
+    sx[0] = ax[0];
+    sy[0] = ay[0];
+    sx[1] = ax[1];
+    sy[1] = ay[1];
+}
+
+// The pair planes as collide_site reads them (the interface of SplitStage):
+// species 0's force and density step are formed together with species 1's,
+// which are kept for the call that follows for species 1.
+template <int SHv>
+struct PairStage {
+    const float2 (*sr)[SW];
+    const float2 (*sp)[SW];
+    mutable float F1x, F1y, d1;
+    __device__ __forceinline__ float density(int k, int cy, int cx) const
+    {
+        const float2 v = sr[cy][cx];
+        return k ? v.y : v.x;
+    }
+    // Eq. (8) + Eq. (9) + rho_k g, as force_at
+    __device__ __forceinline__ void force(const Lat<float> &L, int k, int cx, int cy, float &Fx, float &Fy) const
+    {
+        if (k) {
+            Fx = F1x;
+            Fy = F1y;
+            return;
+        }
+        float s1x[2], s1y[2], s2x[2], s2y[2], s3x[2], s3y[2];
+        q9_pair<SHv>(sp, cx, cy, s1x, s1y);
+        q25_pair<SHv>(sp, cx, cy, s2x, s2y);
+        q9_pair<SHv>(sr, cx, cy, s3x, s3y);   // component j: sums over species j's density
+        const float2 psi = sp[cy][cx], rho = sr[cy][cx];
+        const float G1 = L.G1, G2 = L.G2, GAB = L.GAB;
+        Fx = -G1 * psi.x * s1x[0] - G2 * psi.x * s2x[0] - GAB * rho.x * s3x[1] + rho.x * L.g[0];
+        Fy = -G1 * psi.x * s1y[0] - G2 * psi.x * s2y[0] - GAB * rho.x * s3y[1] + rho.x * L.g[1];
+        F1x = -G1 * psi.y * s1x[1] - G2 * psi.y * s2x[1] - GAB * rho.y * s3x[0] + rho.y * L.g[0];
+        F1y = -G1 * psi.y * s1y[1] - G2 * psi.y * s2y[1] - GAB * rho.y * s3y[0] + rho.y * L.g[1];
+    }
+    template <int EX, int EY>
+    __device__ __forceinline__ float density_step(int k, int cx, int cy) const
+    {
+        if (k) return d1;
+        const float2 a = sr[cy][cx], b = sr[cy + EY][cx + EX];
+        d1 = a.y - b.y;
+        return a.x - b.x;
+    }
+};
+
 // Staged slot (sx, sy) of the h-th position of the halo ring: two rows above,
 // two below, then the two columns on each side of the tile's rows.
 template <int TYv>
@@ -127,7 +235,7 @@ __device__ __forceinline__ bool slot_outside(const Lat<float> &G, int4 t, int sx
 // is full.  Halo slots beyond the lattice were staged by the caller.
 template <int TYv>
 __device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ lats, int4 t, int parity,
-                                               CollideSmem<float, TYv> &sm, const float *__restrict__ pop,
+                                               PairSmem<TYv> &sm, const float *__restrict__ pop,
                                                const float *__restrict__ ref)
 {
     constexpr int SHv = TYv + 2 * HALO, H = SHv, W = kTmaBoxW;
@@ -150,10 +258,8 @@ __device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ la
         ring_slot<TYv>(h, sx, sy);
         if (slot_outside(G, t, sx, sy)) continue;
         const float rA = slot_density(0, sx, sy), rB = slot_density(1, sx, sy);
-        sm.srho[0][sy][sx] = rA;
-        sm.srho[1][sy][sx] = rB;
-        sm.spsi[0][sy][sx] = psi_of<float>(rA);
-        sm.spsi[1][sy][sx] = psi_of<float>(rB);
+        sm.sr[sy][sx] = make_float2(rA, rB);
+        sm.sp[sy][sx] = make_float2(psi_of<float>(rA), psi_of<float>(rB));
     }
     const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
     const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
@@ -169,10 +275,10 @@ __device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ la
         Rn[k] = ref[(k * H + cy) * W + cx + 2];
         const float r = Rn[k] + zeroth_moment<float>(v);
         G.rho[parity ^ 1][(size_t)k * G.plane + c] = r;
-        sm.srho[k][cy][cx] = r;
-        sm.spsi[k][cy][cx] = psi_of<float>(r);
         rn[k] = r;
     }
+    sm.sr[cy][cx] = make_float2(rn[0], rn[1]);
+    sm.sp[cy][cx] = make_float2(psi_of<float>(rn[0]), psi_of<float>(rn[1]));
     // the node's force-free moments: threads without a halo slot form them
     // before the barrier (while the others stage the halo), the others after
     NodeMoments<float> nm;
@@ -181,12 +287,9 @@ __device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ la
     __syncthreads();
     if (!early) node_moments<float>(own, H * W, rn, Rn, nm);
     const bool inner = t.y >= 1 && t.y + TX + 1 <= sm.L.nx && t.z >= 1 && t.z + TYv + 1 <= sm.L.ny;
-    if (inner)
-        collide_site<float, true, SHv, true>(sm.L, G.f[parity ^ 1], sm.srho, sm.spsi, fk, Rn, x, y, cx, cy, own, H * W,
-                                             &nm);
-    else
-        collide_site<float, false, SHv, true>(sm.L, G.f[parity ^ 1], sm.srho, sm.spsi, fk, Rn, x, y, cx, cy, own,
-                                              H * W, &nm);
+    const PairStage<SHv> sg{sm.sr, sm.sp, 0.f, 0.f, 0.f};
+    if (inner) collide_site<float, true, true>(sm.L, G.f[parity ^ 1], sg, fk, Rn, x, y, cx, cy, own, H * W, &nm);
+    else collide_site<float, false, true>(sm.L, G.f[parity ^ 1], sg, fk, Rn, x, y, cx, cy, own, H * W, &nm);
 }
 
 // One block per tile: thread 0 starts the two copies, every thread waits
@@ -202,7 +305,7 @@ __global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
     constexpr int ti = TYv == 2 ? 0 : (TYv == 4 ? 1 : 2);
     extern __shared__ __align__(128) float box[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ CollideSmem<float, TYv> sm;
+    __shared__ PairSmem<TYv> sm;
     const int4 t = tiles[tile_offset + blockIdx.x];
     if (!box_tile(lats[t.x], t, TYv)) {
         if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(err, 2);
@@ -236,7 +339,12 @@ __global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
             for (int h = tid; h < kRing; h += TX * TYv) {
                 int sx, sy;
                 ring_slot<TYv>(h, sx, sy);
-                if (slot_outside(G, t, sx, sy)) stage_slot<float, TYv, false>(G, t, parity, sm, sx, sy);
+                if (slot_outside(G, t, sx, sy)) {
+                    float rA, rB;
+                    slot_densities<float, false>(G, t, parity, sx, sy, rA, rB);
+                    sm.sr[sy][sx] = make_float2(rA, rB);
+                    sm.sp[sy][sx] = make_float2(psi_of<float>(rA), psi_of<float>(rB));
+                }
             }
         }
     }
