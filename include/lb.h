@@ -304,13 +304,14 @@ int lb_batch_set_wait_limit(lb_batch *b, double seconds, int32_t drop_tile);
 #define LB_STATIC_MAX_TILES 32768
 
 /* Observables of an LB_FP64 lattice whose populations live in the caller's
- * device memory, computed without allocating memory of any kind.  No
- * counterpart in the paper: this is a service for callers that may not call
- * cudaMalloc (or anything that allocates) once they run, e.g. an application
- * that owns a fixed device-memory budget or a solver step that must not enter
- * the driver's allocator.
- *   p     lattice parameters (precision must be LB_FP64; p->stream is the
- *         stream the two kernels are launched on, NULL for the default stream)
+ * device memory, computed without allocating memory.  No counterpart in the
+ * paper: this is a service for callers that may not call cudaMalloc (or
+ * anything else that allocates) once they run, e.g. an application that owns
+ * a fixed device-memory budget, or a solver step that must stay out of the
+ * driver's allocator.
+ *   p     lattice parameters, checked as lb_create checks them (precision
+ *         must be LB_FP64; p->stream is the stream the two kernels are
+ *         launched on, NULL for the default stream)
  *   f     device [2][9][ny][nx] FP64 populations, direction order as for
  *         lb_get_populations
  *   cx, cy, R   Laplace probe as for lb_set_probe (R <= 0: none)
@@ -319,15 +320,22 @@ int lb_batch_set_wait_limit(lb_batch *b, double seconds, int32_t drop_tile);
  *         R_eff, umax, finite (1.0 or 0.0), then four zeros; the definitions
  *         are those of lb_obs
  * The scratch is a file-scope device array of LB_STATIC_MAX_TILES x 16
- * doubles (4 MiB) that every GPU which loads the library holds until the
- * process exits.  The first call on a device looks up that array's device
- * address (once per device, with that device current), so make the first
- * call before any stream capture.  Every call shares the array and leaves
- * its contents behind; calls whose kernels overlap on the GPU race on it, so
- * serialise them (one stream, or events).  Asynchronous: obs is written when
- * the stream reaches the kernels.  Returns LB_EINVAL for NULL pointers, a
- * precision other than LB_FP64, invalid sizes or parameters, or a lattice of
- * more than LB_STATIC_MAX_TILES tiles; LB_ECUDA if a launch fails. */
+ * doubles (4 MiB).  CUDA loads the part of the library that holds it on
+ * first use on each device; that is when the driver places the array, which
+ * the device then keeps until the process exits.  Only that first use can
+ * allocate: call lb_observables_static(NULL, NULL, 0, 0, 0, NULL) (f and obs
+ * both NULL: set-up only, nothing is launched, p is ignored) on each device,
+ * with that device current, before the phase in which nothing may be
+ * allocated and before any stream capture; every later call allocates
+ * nothing.  Each call looks the array's device address up again (no
+ * allocation once loaded), so a context reset in between is harmless.
+ * Every call shares the array and leaves its contents behind; calls whose
+ * kernels overlap on the GPU race on it, so serialise them (one stream, or
+ * events).  Asynchronous: obs is written when the stream reaches the
+ * kernels.  Returns LB_EINVAL for a NULL p, f or obs (other than the set-up
+ * form), invalid parameters, a precision other than LB_FP64, a non-finite
+ * probe, or a lattice of more than LB_STATIC_MAX_TILES tiles; LB_ECUDA if
+ * the address lookup or a launch fails. */
 int lb_observables_static(const lb_params *p, const double *f, double cx, double cy, double R, double *obs);
 
 #ifdef __cplusplus

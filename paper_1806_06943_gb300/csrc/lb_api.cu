@@ -1080,6 +1080,7 @@ struct SaveHeader {
 
 namespace lbk {
 void set_last_error(const char *msg) { g_err = msg; }
+int validate_params(const lb_params *p, int index) { return validate(p, index); }
 }  // namespace lbk
 
 struct lb_handle {

@@ -7,6 +7,8 @@
 
 #include "lb_types.h"
 
+struct lb_params;
+
 namespace lbk {
 
 template <typename real>
@@ -87,5 +89,8 @@ constexpr int kAdjSlotCount = 20;
 
 // Record msg as the calling thread's lb_last_error() message.
 void set_last_error(const char *msg);
+// The parameter check of lb_create for lattice `index` of a batch: LB_OK,
+// or LB_EINVAL with the message recorded (lb_api.cu).
+int validate_params(const ::lb_params *p, int index);
 
 }  // namespace lbk

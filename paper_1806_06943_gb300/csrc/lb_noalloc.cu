@@ -17,7 +17,6 @@
 
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "lb.h"
 #include "lb_kernels.cuh"
@@ -29,10 +28,6 @@ namespace {
 // each: 32768 * 16 * 8 bytes = 4 MiB of device memory.
 constexpr int kMaxTiles = LB_STATIC_MAX_TILES;
 static __device__ __align__(256) double g_partials[(size_t)kMaxTiles * lbk::kAccStride];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-double *g_partials_ptr[kMaxDevices] = {nullptr};
 
 // Densities of the tile plus its halo from the populations, then psi.
 __device__ __forceinline__ void stage_from_pops(const lbk::Lat<double> &L, const double *__restrict__ f, int x0, int y0,
@@ -210,36 +205,34 @@ int set_fail(int code, const char *msg)
 
 extern "C" int lb_observables_static(const lb_params *p, const double *f, double cx, double cy, double R, double *obs)
 {
-    if (!p || !f || !obs) return set_fail(LB_EINVAL, "lb_observables_static: NULL argument");
-    if (p->precision != LB_FP64) return set_fail(LB_EINVAL, "lb_observables_static: populations must be LB_FP64");
-    if (p->nx < 5 || p->ny < 5) return set_fail(LB_EINVAL, "lb_observables_static: nx and ny must be >= 5");
-    if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5) || !std::isfinite(p->tau[0]) || !std::isfinite(p->tau[1]))
-        return set_fail(LB_EINVAL, "lb_observables_static: tau must be finite and > 1/2");
-    if (p->walls != LB_PERIODIC && p->walls != LB_WALLS_Y)
-        return set_fail(LB_EINVAL, "lb_observables_static: walls must be 0 or 1");
-    if (!std::isfinite(cx) || !std::isfinite(cy) || !std::isfinite(R))
-        return set_fail(LB_EINVAL, "lb_observables_static: non-finite probe");
-    const long long tiles_x = (p->nx + lbk::TX - 1) / lbk::TX, tiles_y = (p->ny + lbk::TY - 1) / lbk::TY;
+    // set-up only: load this file's module on the current device (the driver
+    // places g_partials then) and resolve the array's address; nothing runs
+    const bool setup_only = !f && !obs;
+    if (!setup_only) {
+        if (!p || !f || !obs) return set_fail(LB_EINVAL, "lb_observables_static: NULL argument");
+        if (lbk::validate_params(p, 0) != LB_OK) return LB_EINVAL;   // message recorded by the check
+        if (p->precision != LB_FP64) return set_fail(LB_EINVAL, "lb_observables_static: populations must be LB_FP64");
+        if (!std::isfinite(cx) || !std::isfinite(cy) || !std::isfinite(R))
+            return set_fail(LB_EINVAL, "lb_observables_static: non-finite probe");
+    }
+    const long long tiles_x = setup_only ? 0 : (p->nx + lbk::TX - 1) / lbk::TX;
+    const long long tiles_y = setup_only ? 0 : (p->ny + lbk::TY - 1) / lbk::TY;
     if (tiles_x * tiles_y > kMaxTiles)
         return set_fail(LB_EINVAL, "lb_observables_static: lattice exceeds LB_STATIC_MAX_TILES tiles of 32x4 nodes");
 
-    int dev = 0;
-    cudaError_t ce = cudaGetDevice(&dev);
-    if (ce != cudaSuccess) return set_fail(LB_ECUDA, "lb_observables_static: cudaGetDevice failed");
-    if (dev < 0 || dev >= kMaxDevices) return set_fail(LB_EINVAL, "lb_observables_static: device index too large");
-    double *scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_partials_ptr[dev]) {
-            // the host name of g_partials is not a device address: ask the
-            // runtime for this device's address once, with the device current
-            void *ptr = nullptr;
-            ce = cudaGetSymbolAddress(&ptr, g_partials);
-            if (ce != cudaSuccess) return set_fail(LB_ECUDA, "lb_observables_static: cudaGetSymbolAddress failed");
-            g_partials_ptr[dev] = (double *)ptr;
-        }
-        scratch = g_partials_ptr[dev];
+    // The host name g_partials is only a stand-in for the array, not a device
+    // address: ask the runtime for the address on the current device.  The
+    // lookup is repeated on every call, so a context torn down and created
+    // again (cudaDeviceReset) never leaves a stale address behind; once the
+    // module is loaded on the device the lookup allocates nothing.
+    void *ptr = nullptr;
+    cudaError_t ce = cudaGetSymbolAddress(&ptr, g_partials);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return set_fail(LB_ECUDA, "lb_observables_static: cudaGetSymbolAddress failed");
     }
+    if (setup_only) return LB_OK;
+    double *scratch = (double *)ptr;
 
     lbk::Lat<double> L;
     std::memset(&L, 0, sizeof L);
