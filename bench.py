@@ -15,9 +15,18 @@ site update advances both species.  With --gpus N (torchrun), every rank
 advances its own copy of the batch (weak scaling, no data-path collective);
 the value is the sum over ranks divided by the slowest rank's time.
 
-Side legs (skipped with --quick): the same batch in FP64, the 4096x4096
-dense emulsion in FP32 and FP64, an end-to-end job through the public API
-with host buffers, and the CPU oracle timed on a bounded sample.
+Roofline: the step kernel's algorithmic bytes (the populations read and
+written once: 144 B per node in FP32, 288 B in FP64) per launch over its
+CUDA-event time, against the measured copy bandwidth; the design's own
+byte count (160 B per node in FP32, with the reference densities) beside
+it.  The FP64 kernel is bound by the FP64 pipe and is reported against the
+device's measured FP64 FMA rate.
+
+Side legs (skipped with --quick): the Laplace fit of the sweep after 20000
+steps, the same batch in FP64, the 4096x4096 dense emulsion in FP32 and
+FP64, an end-to-end job through the public API with host buffers, the
+adjoint, and the CPU oracle timed on a bounded sample on one and on every
+host core.
 ``--impl reference`` times the CPU oracle alone as the reference arm.
 """
 from __future__ import annotations
@@ -36,10 +45,21 @@ sys.path.insert(0, ROOT)
 
 C6 = dict(G_AB=3.0, G1=-7.4, G2=6.4)
 FLUSH_BYTES = 256 << 20
-# algorithmic bytes per node and launch (FP32 offset / FP64 plain):
+# Algorithmic bytes per node update (FP32 offset / FP64 plain): the 2 x 9
+# populations read once and written once.  The roofline fraction is taken
+# on these.
+FLOOR_BYTES = {1: 144, 0: 288}
+# Bytes each kernel of this design moves per node and launch, reported beside
+# the floor: the FP32 form also reads the node's 2 reference densities and
+# writes its 2 densities (the next step's references).
 BYTES_FUSED = {1: 160, 0: 288}     # one-pass: 18 pops read + 18 written (+ 2 reference rho read, 2 written)
 BYTES_COLLIDE = {1: 160, 0: 304}   # two-pass fused kernel: 18 pops read + 18 written + 2 rho read (+ 2 reference rho read)
 BYTES_DENSITY = {1: 88, 0: 160}    # density pass: 18 pops read + 2 rho written (+ 2 reference rho read)
+# FP64 operations per node of the FP64 one-pass kernel (k_fused<double, 8>),
+# DADD + DMUL + 2 DFMA thread instructions per node from ncu on the 512^2
+# dense emulsion (profiles/k_fused_fp64_dense_emulsion_512.md); None until
+# measured on the current kernel.
+FP64_FLOPS_PER_NODE = None
 
 
 def parse():
@@ -50,7 +70,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--quick", action="store_true", help="main leg only")
     ap.add_argument("--workload", default="laplace_sweep_24",
-                    choices=["laplace_sweep_24", "dense_emulsion_4096", "dense_emulsion_2048"],
+                    choices=["laplace_sweep_24", "dense_emulsion_4096", "dense_emulsion_2048", "dense_emulsion_512"],
                     help="main-leg workload (the dense emulsions are single periodic lattices)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--mode", default="tma", choices=["tma", "fused", "launch"],
@@ -221,14 +241,39 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def hbm_roofline(kname, units, ms, peak, peak_kind, floor_b, design_b, traffic):
+    """Roofline of an HBM-bound step kernel: achieved = algorithmic bytes per
+    node (the populations read and written once) x nodes per launch / the
+    launch's CUDA-event time; the design's own byte count beside it."""
+    ach = floor_b * units / (ms * 1e-3) / 1e9
+    des = design_b * units / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (burst)",
+            "algorithmic_bytes_per_site": floor_b, "units_per_launch": units, "ms_per_launch": ms,
+            "design_bytes_per_site": design_b, "design_achieved": des, "design_frac": des / peak}
+
+
+def alu_roofline(kname, units, ms, peak_tflops, hbm_peak):
+    """Roofline of the FP64 step kernel, bound by the FP64 pipe: FP64
+    operations per node (ncu count) x nodes / launch time against the
+    measured FP64 FMA rate of the device."""
+    ach = FP64_FLOPS_PER_NODE * units / (ms * 1e-3) / 1e12 if FP64_FLOPS_PER_NODE else None
+    return {"bound": "alu", "kernel": kname, "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": (ach / peak_tflops) if (ach and peak_tflops) else None, "traffic": None,
+            "peak_source": "measured FP64 FMA throughput of this device (lb_device_fp64_peak)",
+            "flops_per_site": FP64_FLOPS_PER_NODE, "units_per_launch": units, "ms_per_launch": ms,
+            "hbm_frac_floor": FLOOR_BYTES[0] * units / (ms * 1e-3) / 1e9 / hbm_peak}
+
+
 # ---- CPU oracle timing -------------------------------------------------------------
 
-def oracle_sample(target_s: float):
+def oracle_sample(target_s: float, threads: int = 1):
     """The oracle advancing lattice 0 of the sweep (128x128, R=10, ratio 1)
-    for as many steps as fit in about target_s seconds; returns MLUPS."""
+    on `threads` host threads (its OpenMP row loops) for as many steps as fit
+    in about target_s seconds; returns (MLUPS, description, steps, threads)."""
     import oracle
-    specs, _ = None, None
     from paper_1806_06943_gb300 import workloads as W
+    used = oracle.set_threads(threads)
     s0 = W.laplace_sweep_specs()[0]
     rho = W.droplet(s0["nx"], s0["ny"], s0["R"], seed=W.BASE_SEED + 1)
     sim = oracle.OracleSim(s0["nx"], s0["ny"], tau=s0["tau"], **C6)
@@ -241,7 +286,9 @@ def oracle_sample(target_s: float):
     sim.step(n)
     dt = time.perf_counter() - t0
     sites = s0["nx"] * s0["ny"]
-    return sites * n / dt / 1e6, f"lattice 0 of the sweep ({s0['nx']}x{s0['ny']}, R={s0['R']:g}), {n} steps, {dt:.1f} s", n
+    return (sites * n / dt / 1e6,
+            f"lattice 0 of the sweep ({s0['nx']}x{s0['ny']}, R={s0['R']:g}), {n} steps, {dt:.1f} s, {used} threads",
+            n, used)
 
 
 def run_reference(args):
@@ -250,11 +297,12 @@ def run_reference(args):
         return 0
     import oracle
     from paper_1806_06943_gb300 import workloads as W
+    cores = oracle.set_threads(os.cpu_count() or 1)   # every host core (OpenMP row loops)
     s0 = W.laplace_sweep_specs()[0]
     rho = W.droplet(s0["nx"], s0["ny"], s0["R"], seed=W.BASE_SEED + 1)
     sim = oracle.OracleSim(s0["nx"], s0["ny"], tau=s0["tau"], **C6)
     sim.set_fields(rho)
-    steps_per = 20   # each benchmark step: 20 time steps of lattice 0 (bounded sample)
+    steps_per = 20 * cores   # each benchmark step: 20 time steps per core of lattice 0 (bounded sample)
     for _ in range(args.warmup):
         sim.step(steps_per)
     t0 = time.perf_counter()
@@ -267,10 +315,12 @@ def run_reference(args):
         "impl": "reference", "metric": "2-species MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "laplace_sweep_24", "sample": "lattice 0 (128x128, R=10, ratio 1), 20 time steps per step",
+        "config": {"workload": "laplace_sweep_24",
+                   "sample": f"lattice 0 (128x128, R=10, ratio 1), {steps_per} time steps per step",
                    "precision": "fp64 (CPU oracle)"},
-        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"lattice 0 of the sweep, {steps_per} time steps per benchmark step"},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"lattice 0 of the sweep, {steps_per} time steps per benchmark step, "
+                                   f"{cores} threads"},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -303,6 +353,7 @@ def main():
     sptr = stream.cuda_stream
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     peak, peak_kind = measured_peaks()
+    fp64_peak = lb.device_fp64_peak(4096)
 
     extra_cfg = {}
     if args.workload == "laplace_sweep_24":
@@ -359,19 +410,12 @@ def main():
                    "timing": "CUDA events per kernel on the launching stream", "parallelism": f"replicas x{world}"},
         "clocks": clk,
         "gpu_launches": gpu_launches,
-        "roofline": {
-            "bound": "hbm", "kernel": kname,
-            "achieved": kbytes[prec] * sites / (ms[1] * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-            "frac": kbytes[prec] * sites / (ms[1] * 1e-3) / 1e9 / peak,
-            "traffic": kernel_traffic(args.workload, kname) if prec == lb.LB_FP32 else None,
-            "peak_source": f"{peak_kind} hbm_gbs (burst)",
-            "algorithmic_bytes_per_site": kbytes[prec], "units_per_launch": sites,
-            "ms_per_launch": ms[1],
-        },
+        "roofline": (hbm_roofline(kname, sites, ms[1], peak, peak_kind, FLOOR_BYTES[prec], kbytes[prec],
+                                  kernel_traffic(args.workload, kname))
+                     if prec == lb.LB_FP32 else alu_roofline(kname, sites, ms[1], fp64_peak, peak)),
         "mode": args.mode,
         "wall_s_timed": t_wall,
-        "observables_after": {"finite": all(o["finite"] == 1.0 for o in obs),
-                              "gamma_fit_ratio1": None},
+        "observables_after": {"finite": all(o["finite"] == 1.0 for o in obs)},
     }
 
     if not args.quick and args.workload == "laplace_sweep_24" and prec == lb.LB_FP32:
@@ -406,17 +450,40 @@ def main():
                             "trial_ms_per_step": tuned_ms,
                             "sustained_mlups": sites * 256 / (ev0.elapsed_time(ev1) * 1e-3) / 1e6}
 
-        # Laplace fit at ratio 1 after the run so far (not converged; sanity only)
+        # the sweep's own observable: 20000 steps of all 24 drops (FP32, the
+        # configured mode), then the Laplace law dp = gamma / R_eff + c fitted
+        # per viscosity ratio
+        bl = make_batch(lb, specs, fields, lb.LB_FP32, sptr)
+        bl.set_config(mode, args.tile_height)
+        t0 = time.perf_counter()
+        bl.step(20000)
+        obs_l = bl.observables()
+        t_l = time.perf_counter() - t0
+        fits = {}
+        for ratio in sorted({sp["ratio"] for sp in specs}):
+            pts = [(1.0 / o["R_eff"], o["dp"]) for sp, o in zip(specs, obs_l) if sp["ratio"] == ratio]
+            xs, ys = [p[0] for p in pts], [p[1] for p in pts]
+            n_, mx, my = len(xs), sum(xs) / len(xs), sum(ys) / len(ys)
+            sxx = sum((x - mx) ** 2 for x in xs)
+            gamma = sum((x - mx) * (y - my) for x, y in zip(xs, ys)) / sxx
+            c0 = my - gamma * mx
+            ss_res = sum((y - gamma * x - c0) ** 2 for x, y in zip(xs, ys))
+            ss_tot = sum((y - my) ** 2 for y in ys)
+            fits[f"ratio_{ratio:g}"] = {"gamma": gamma, "intercept": c0, "r2": 1 - ss_res / ss_tot, "drops": n_}
+        out["laplace_fit_20k"] = {"steps": 20000, "seconds": t_l, "precision": "fp32", "fits": fits,
+                                  "finite": all(o["finite"] == 1.0 for o in obs_l)}
+        del bl
+
         # FP64 on the same batch
         b64 = make_batch(lb, specs, fields, lb.LB_FP64, sptr)
-        b64.set_config(lb.LB_MODE_FUSED if mode == lb.LB_MODE_TMA else mode, 4)
+        b64.set_config(lb.LB_MODE_FUSED if mode == lb.LB_MODE_TMA else mode, 8)
         b64.profile(3, flush.data_ptr(), FLUSH_BYTES)
         k64 = max(10, args.steps // 4)
         ms64 = b64.profile(k64, flush.data_ptr(), FLUSH_BYTES)
         out["fp64_same_workload"] = {
             "mlups": sites / (ms64[2] * 1e-3) / 1e6, "ms_per_step": ms64[2], "steps": k64,
             "kernel_ms": ms64[1], "density_ms": ms64[0],
-            "kernel_achieved_gbs": kbytes[0] * sites / (ms64[1] * 1e-3) / 1e9,
+            "roofline": alu_roofline("k_fused<double, 8>", sites, ms64[1], fp64_peak, peak),
         }
         out["fp32_over_fp64"] = value / out["fp64_same_workload"]["mlups"]
         del b64
@@ -437,13 +504,16 @@ def main():
             L.set_config(lb.LB_MODE_LAUNCH, 4)
             L.profile(2, flush.data_ptr(), FLUSH_BYTES)
             m2 = L.profile(k, flush.data_ptr(), FLUSH_BYTES)
+            bk = (f"k_fused_tma<{args.tile_height}>" if big_mode == lb.LB_MODE_TMA else
+                  f"k_fused<{'float' if prec else 'double'}, {args.tile_height}>")
             big[name] = {"mode": ["launch", "persistent", "fused", "tma"][big_mode], "tile_height": args.tile_height,
                          "mlups": n4 / (m[2] * 1e-3) / 1e6, "ms_per_step": m[2], "steps": k,
-                         "fused_achieved_gbs": BYTES_FUSED[prec] * n4 / (m[1] * 1e-3) / 1e9,
-                         "fused_frac_of_measured_hbm": BYTES_FUSED[prec] * n4 / (m[1] * 1e-3) / 1e9 / peak,
+                         "roofline": (hbm_roofline(bk, n4, m[1], peak, peak_kind, FLOOR_BYTES[prec], BYTES_FUSED[prec],
+                                                   kernel_traffic("dense_emulsion_4096", bk))
+                                      if prec == lb.LB_FP32 else alu_roofline(bk, n4, m[1], fp64_peak, peak)),
                          "two_pass_mlups": n4 / (m2[2] * 1e-3) / 1e6, "collide_ms": m2[1], "density_ms": m2[0],
-                         "collide_frac_of_measured_hbm": BYTES_COLLIDE[prec] * n4 / (m2[1] * 1e-3) / 1e9 / peak,
-                         "step_effective_gbs_floor": (144 if prec else 288) * n4 / (m[2] * 1e-3) / 1e9}
+                         "collide_frac_floor": FLOOR_BYTES[prec] * n4 / (m2[1] * 1e-3) / 1e9 / peak,
+                         "collide_frac_design": BYTES_COLLIDE[prec] * n4 / (m2[1] * 1e-3) / 1e9 / peak}
             del L
         out["large_dense_4096"] = big
 
@@ -499,8 +569,11 @@ def main():
 
         # CPU oracle on a bounded sample (rank 0 only)
         if rank == 0 and world == 1:
-            v, sample, n = oracle_sample(12.0)
-            out["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample}
+            ncores = os.cpu_count() or 1
+            v1, sample1, _, _ = oracle_sample(8.0, 1)
+            vn, samplen, _, used = oracle_sample(8.0, ncores)
+            out["cpu_baseline"] = {"value": vn, "unit": "MLUPS", "cores": used, "kind": "oracle", "sample": samplen,
+                                   "one_core": {"value": v1, "sample": sample1}, "nproc": ncores}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

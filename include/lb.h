@@ -297,6 +297,17 @@ int lb_batch_autotune(lb_batch *b, int32_t trial_steps, const char *cache_path, 
  * LB_ETIMEOUT; -1 turns the hook off. */
 int lb_batch_set_wait_limit(lb_batch *b, double seconds, int32_t drop_tile);
 
+/* ---- device diagnostics ------------------------------------------------------ */
+
+/* Measured FP64 fused multiply-add throughput of the current device in
+ * TFLOP/s (2 flops per FMA): independent FMA chains on every SM at full
+ * occupancy, trips x 128 FMAs per thread, best of five timed launches after
+ * a warm-up, CUDA events on a stream of its own.  Not part of the method: it
+ * is the denominator of the FP64 step's roofline, which is bound by the FP64
+ * pipe rather than by memory.  Allocates and frees a few KB; synchronises.
+ * LB_EINVAL for trips < 1 or a NULL tflops, LB_ECUDA on a failed CUDA call. */
+int lb_device_fp64_peak(int32_t trips, double *tflops);
+
 /* ---- observables without any allocation ------------------------------------ */
 
 /* Largest lattice lb_observables_static accepts, in tiles of 32 x 4 nodes

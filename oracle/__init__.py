@@ -3,7 +3,9 @@ method (Fei et al., arXiv:1806.06943).
 
 TEST INFRASTRUCTURE ONLY: the test suite, the package smoke check and the
 benchmark's CPU-baseline leg are the only callers.  The method itself lives in
-``oracle.c`` (single-threaded, no fused multiply-add, libm ``exp``); this file
+``oracle.c`` (no fused multiply-add, libm ``exp``; the row loops of a time
+step optionally on several OpenMP threads, with results bitwise those of one
+thread); this file
 compiles it with the host C compiler and marshals arguments through ctypes.
 It shares no code with the CUDA path.
 """
@@ -26,13 +28,23 @@ CFLAGS = ["-O2", "-ffp-contract=off", "-std=c99", "-fPIC", "-shared"]
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so next to it (only when stale)."""
+    """Compile oracle.c into liboracle.so next to it (only when stale), with
+    OpenMP where the compiler offers it (the row loops may then run on several
+    threads, with bitwise the same results), else without."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         cc = os.environ.get("CC", "cc")
-        subprocess.run([cc, *CFLAGS, _SRC, "-o", tmp, "-lm"], check=True)
+        r = subprocess.run([cc, *CFLAGS, "-fopenmp", _SRC, "-o", tmp, "-lm"], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.run([cc, *CFLAGS, _SRC, "-o", tmp, "-lm"], check=True)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's row loops (n <= 0: keep); returns the count in
+    use, 1 when built without OpenMP."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 class OrcParams(ctypes.Structure):
@@ -72,6 +84,8 @@ def _load():
             lib.orc_guo.argtypes = [d, d, d, d, d, dp]
             lib.orc_tables.argtypes = [dp, P(ctypes.c_int32), P(ctypes.c_int32), dp,
                                        P(ctypes.c_int32), P(ctypes.c_int32)]
+            lib.orc_set_threads.restype = ctypes.c_int
+            lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_bulk_pressure.restype = d
             lib.orc_bulk_pressure.argtypes = [P(OrcParams), d, d]
             _lib = lib

@@ -1,5 +1,5 @@
 /*
- * oracle.c -- plain, slow, single-threaded FP64 restatement of the two-range
+ * oracle.c -- plain, slow FP64 restatement of the two-range
  * pseudopotential lattice Boltzmann method for binary mixtures with tunable
  * viscosity ratio (Fei, Scagliarini, Montessori, Lauricella, Succi, Luo,
  * "Mesoscopic model for soft flowing systems with tunable viscosity ratio",
@@ -15,9 +15,11 @@
  * velocity, (8) competing intra-species force, (9) inter-species repulsion,
  * (11) bulk equation of state, (19) layered Poiseuille profile.
  *
- * Build: cc -O2 -ffp-contract=off -std=c99 -fPIC -shared oracle.c -lm
+ * Build: cc -O2 -ffp-contract=off -std=c99 -fPIC -shared [-fopenmp] oracle.c -lm
  * (no fused multiply-add, libm exp), so every operation below rounds once,
- * in the order it is written.
+ * in the order it is written.  With OpenMP the row loops of a time step run
+ * on several threads; no sum crosses rows, so the results do not depend on
+ * the thread count.
  *
  * Readings where the paper is silent or garbled (each listed with its reason
  * in the design notes):
@@ -37,6 +39,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_PI 3.14159265358979323846
 
@@ -192,6 +197,7 @@ void orc_tables(double w[9], int32_t ex[9], int32_t ey[9], double p[25], int32_t
 static void density(orc_sim *s)
 {
     for (int k = 0; k < 2; ++k)
+#pragma omp parallel for schedule(static)
         for (int y = 0; y < s->p.ny; ++y)
             for (int x = 0; x < s->p.nx; ++x) {
                 double r = 0.0;
@@ -207,6 +213,7 @@ static void fill_extended(orc_sim *s)
 {
     int nx = s->p.nx, ny = s->p.ny;
     for (int k = 0; k < 2; ++k)
+#pragma omp parallel for schedule(static)
         for (int y = -2; y < ny + 2; ++y)
             for (int x = 0; x < nx; ++x) {
                 double r;
@@ -263,6 +270,7 @@ static void forces(orc_sim *s)
     density(s);
     fill_extended(s);
     for (int k = 0; k < 2; ++k)
+#pragma omp parallel for schedule(static)
         for (int y = 0; y < s->p.ny; ++y)
             for (int x = 0; x < s->p.nx; ++x)
                 force_at(s, k, x, y, &s->force[FOIDX(s, k, 0, x, y)], &s->force[FOIDX(s, k, 1, x, y)]);
@@ -295,6 +303,8 @@ static void step_once(orc_sim *s)
 {
     int nx = s->p.nx, ny = s->p.ny;
     forces(s);
+    /* every (species, direction, node) of fn is written by exactly one site */
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             double rho[2], m[2][2], ueq[2];
@@ -320,6 +330,21 @@ static void step_once(orc_sim *s)
     s->f = s->fn;
     s->fn = tmp;
     s->t += 1;
+}
+
+/* Threads of the row loops (OpenMP, when the library was built with it):
+ * each node's arithmetic is the same whatever thread runs it, so the results
+ * are bitwise those of one thread.  Returns the count in use (1 without
+ * OpenMP). */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 void orc_step(orc_sim *s, long n)

@@ -32,6 +32,7 @@ UNITS = {
     "lb_tma.cu": [],
     "lb_noalloc.cu": ["-fmad=false"],
     "lb_adjoint.cu": ["-fmad=false"],
+    "lb_device.cu": [],
 }
 
 

@@ -110,7 +110,15 @@ SIGNATURES = {
     "lb_batch_autotune": (ctypes.c_int, [_vp, _i32, ctypes.c_char_p, _dp]),
     "lb_batch_set_wait_limit": (ctypes.c_int, [_vp, _d, _i32]),
     "lb_observables_static": (ctypes.c_int, [_P(lb_params), _vp, _d, _d, _d, _vp]),
+    "lb_device_fp64_peak": (ctypes.c_int, [_i32, _dp]),
 }
+
+
+def device_fp64_peak(trips: int = 4096) -> float:
+    """Measured FP64 FMA throughput of the current device, TFLOP/s."""
+    v = ctypes.c_double()
+    _check(LIB.lb_device_fp64_peak(int(trips), ctypes.byref(v)))
+    return v.value
 
 
 def header_functions() -> list[str]:

@@ -135,106 +135,210 @@ def layered_channel(nx, ny, a, hi=MAJORITY, lo=MINORITY, noise=0.0, seed=BASE_SE
     return _fill(np.ascontiguousarray(m), seed, hi, lo, noise)
 
 
-def hex_emulsion(nx, ny, phi, R=12.0, spread=2.0, gap=3.0, walls=True, seed=BASE_SEED, noise=NOISE):
-    """Non-overlapping droplets on a jittered hexagonal lattice, periodic in x
-    (and in y unless walls).  Returns (rho, centres, radii, achieved_phi).
-
-    The spacing is chosen for the target area fraction phi at mean radius R;
-    each radius is drawn from U[R - spread, R + spread] and clipped so any two
-    neighbours keep at least `gap` nodes between them; each centre is jittered
-    inside the slack that remains."""
-    rng = np.random.default_rng(seed)
-    H = ny - 2 * gap if walls else ny
-    s = math.sqrt(2.0 * math.pi * R * R / (math.sqrt(3.0) * phi))
-    ncol = max(1, int(round(nx / s)))
-    sx = nx / ncol
-    dy = sx * math.sqrt(3.0) / 2.0
+def _hex_rows(ny, nrow, R, gap, walls):
+    """Row spacing and first row of nrow droplet rows: between the walls the
+    rows span the band the drops' centres may occupy, periodic rows are
+    evenly spaced."""
     if walls:
-        nrow = max(1, int(math.floor((H - 2 * (R + 0) ) / dy)) + 1)
-        span = (nrow - 1) * dy
-        y0 = (ny - 1) / 2.0 - span / 2.0
-    else:
-        nrow = max(2, 2 * int(round(ny / dy / 2)))
-        dy = ny / nrow
-        y0 = dy / 2
-    rmax_pair = (min(sx, math.hypot(sx / 2, dy)) - gap) / 2.0
+        lo_c, hi_c = gap - 0.5 + R, ny - 0.5 - gap - R
+        dy = (hi_c - lo_c) / (nrow - 1) if nrow > 1 else 0.0
+        return dy, (lo_c if nrow > 1 else (ny - 1) / 2.0)
+    dy = ny / nrow
+    return dy, dy / 2
+
+
+def _hex_rmax(nx, ny, nrow, ncol, R, gap, walls):
+    """Largest radius two neighbouring sites of the lattice can hold with
+    `gap` nodes between them."""
+    sx = nx / ncol
+    dy, _ = _hex_rows(ny, nrow, R, gap, walls)
+    d = sx if nrow == 1 else min(sx, math.hypot(sx / 2, dy))
+    if ncol == 1:
+        d = dy if nrow > 1 else float(min(nx, ny))
+    if not walls and nrow == 2:
+        d = min(d, math.hypot(sx / 2, dy))
+    return (d - gap) / 2.0
+
+
+def _hex_layout(nx, ny, nrow, ncol, R, spread, gap, walls, seed):
+    """Centres and radii of a jittered hexagonal lattice of nrow x ncol
+    droplet sites (see hex_emulsion)."""
+    rng = np.random.default_rng(seed)
+    sx = nx / ncol
+    dy, y0 = _hex_rows(ny, nrow, R, gap, walls)
+    rmax_pair = _hex_rmax(nx, ny, nrow, ncol, R, gap, walls)
     centres, radii = [], []
     for j in range(nrow):
         for i in range(ncol):
-            r = float(rng.uniform(R - spread, R + spread))
-            r = min(r, rmax_pair)
+            r = min(float(rng.uniform(R - spread, R + spread)), rmax_pair)
             cx = (i + 0.5 * (j % 2)) * sx + sx / 4
             cy = y0 + j * dy
-            if walls:
-                lo_y, hi_y = gap - 0.5 + r, ny - 0.5 - gap - r
-                if hi_y < lo_y:
-                    continue
-            slack = max(0.0, rmax_pair - r)
             ang = rng.uniform(0, 2 * math.pi)
-            d = rng.uniform(0, slack)
+            d = rng.uniform(0, max(0.0, rmax_pair - r))
+            if walls:
+                r = min(r, (ny - 2 * gap) / 2.0)
+                if j == 0 or j == nrow - 1:
+                    r = min(r, R)       # the outer rows sit R + gap from the walls
+                lo_y, hi_y = gap - 0.5 + r, ny - 0.5 - gap - r
+                if r <= 0 or hi_y < lo_y:
+                    continue
             cx += d * math.cos(ang)
             cy += d * math.sin(ang)
             if walls:
                 cy = min(max(cy, lo_y), hi_y)
             centres.append((cx % nx, cy if walls else cy % ny))
             radii.append(r)
-    rho = droplets(nx, ny, centres, radii, seed=seed, noise=noise, periodic=not walls)
-    achieved = float((rho[0] > 0.5).mean())
-    return rho, centres, radii, achieved
+    return centres, radii
+
+
+def _clipped_r2(a, b, m):
+    """E[min(r, m)^2] for r uniform on [a, b]."""
+    if b <= a:
+        return min(a, m) ** 2
+    if m >= b:
+        return (b ** 3 - a ** 3) / (3.0 * (b - a))
+    if m <= a:
+        return m * m
+    return ((m ** 3 - a ** 3) / 3.0 + m * m * (b - m)) / (b - a)
+
+
+def hex_emulsion(nx, ny, phi, R=12.0, spread=2.0, gap=3.0, walls=True, seed=BASE_SEED, noise=NOISE,
+                 min_gap=2.0):
+    """Non-overlapping droplets on a jittered hexagonal lattice, periodic in x
+    (and in y unless walls), at area fraction phi.  Returns (rho, centres,
+    radii, achieved_phi).
+
+    Each radius is drawn from U[R - spread, R + spread] and clipped so that
+    any two neighbours keep at least `gap` nodes between them (and the walls
+    `gap` nodes from every drop); each centre is jittered inside the slack
+    that remains.  Between walls the rows span the band the centres may
+    occupy.  The numbers of rows and columns are searched so that the
+    rasterised area fraction comes closest to phi, among near ties the lattice
+    that clips the fewest radii.  Where even the densest lattice with this gap
+    stays more than 0.01 below phi, the gap is narrowed in steps of 0.5 down to
+    min_gap."""
+    area = float(nx * ny)
+
+    def raster(nr, nc, gp):
+        c, r = _hex_layout(nx, ny, nr, nc, R, spread, gp, walls, seed)
+        rho = droplets(nx, ny, c, r, seed=seed, noise=noise, periodic=not walls)
+        return rho, c, r, float((rho[0] > 0.5).mean())
+
+    best = None
+    gp = gap
+    while True:
+        cands = []
+        for nr in range(1, max(2, int(ny / (2.0 * (R - spread) + gp)) + 2)):
+            if not walls and nr % 2:
+                continue
+            for nc in range(1, max(2, int(nx / (2.0 * (R - spread) + gp)) + 2)):
+                m = _hex_rmax(nx, ny, nr, nc, R, gp, walls)
+                if m < R - spread:
+                    continue
+                est = math.pi * nr * nc * _clipped_r2(R - spread, R + spread, m) / area
+                cands.append((nr, nc, m, est))
+        want = phi
+        for _ in range(3):      # aim the analytic estimate, correct by the raster's bias
+            if not cands:
+                break
+            near = [c for c in cands if abs(c[3] - want) <= 0.004]
+            nr, nc, _, _ = max(near, key=lambda c: c[2]) if near else min(cands, key=lambda c: abs(c[3] - want))
+            out = raster(nr, nc, gp)
+            if best is None or abs(out[3] - phi) < abs(best[3] - phi):
+                best = out
+            if abs(out[3] - phi) <= 0.005:
+                break
+            want += phi - out[3]
+        if (best is not None and best[3] >= phi - 0.01) or gp - 0.5 < min_gap - 1e-9:
+            if best is None:
+                raise ValueError("no droplet fits the lattice")
+            return best
+        gp -= 0.5
 
 
 def random_emulsion(nx, ny, phi, rmin=8.0, rmax=20.0, gap=2.0, seed=BASE_SEED, noise=NOISE,
-                    max_tries=60):
+                    max_tries=300):
     """Polydisperse periodic emulsion: radii U[rmin, rmax] placed largest
-    first by random sequential addition (cell-list overlap test), then a fill
-    with rmin droplets until phi or the attempt budget is reached.
+    first by random sequential addition (up to max_tries uniform candidate
+    centres per drop; the first one that keeps `gap` nodes to every placed
+    drop wins), then a fill with rmin droplets until phi is reached or
+    20 max_tries candidates in a row fail.  The overlap test looks at the
+    drops of the 3 x 3 cells of a cell list around each candidate.
     Returns (rho, centres, radii, achieved_phi)."""
     rng = np.random.default_rng(seed)
     area = nx * ny
     target = phi * area
     cell = 2 * rmax + gap
     ncx, ncy = max(1, int(nx // cell)), max(1, int(ny // cell))
-    grid: dict = {}
+    # drops per cell: centres of drops of radius >= rmin keep 2 rmin + gap
+    # apart, so a cell holds at most K of them; empty slots sit far away
+    K = int((cell / (2 * rmin + gap) + 1.5) ** 2) + 1
+    far = 1e30
+    slots = np.full((ncy, ncx, K, 3), far)
+    slots[..., 2] = 0.0
+    count = np.zeros((ncy, ncx), dtype=np.int64)
     centres, radii = [], []
     filled = 0.0
+    offs = np.array([-1, 0, 1])
 
-    def fits(cx, cy, r):
-        gx, gy = int(cx / nx * ncx) % ncx, int(cy / ny * ncy) % ncy
-        for ox in (-1, 0, 1):
-            for oy in (-1, 0, 1):
-                for (qx, qy, qr) in grid.get(((gx + ox) % ncx, (gy + oy) % ncy), ()):
-                    ddx = abs(cx - qx); ddx = min(ddx, nx - ddx)
-                    ddy = abs(cy - qy); ddy = min(ddy, ny - ddy)
-                    if ddx * ddx + ddy * ddy < (r + qr + gap) ** 2:
-                        return False
-        return True
+    def first_fit(cand, r):
+        """Index of the first candidate centre that fits, or -1 (tested in
+        growing chunks: early drops fit at once)."""
+        lo = 0
+        for hi in (4, 16, 64, len(cand)):
+            hi = min(hi, len(cand))
+            if hi <= lo:
+                continue
+            i = fit_chunk(cand[lo:hi], r)
+            if i >= 0:
+                return lo + i
+            lo = hi
+        return -1
 
-    def add(cx, cy, r):
-        gx, gy = int(cx / nx * ncx) % ncx, int(cy / ny * ncy) % ncy
-        grid.setdefault((gx, gy), []).append((cx, cy, r))
-        centres.append((cx, cy))
-        radii.append(r)
+    def fit_chunk(cand, r):
+        gx = (cand[:, 0] / nx * ncx).astype(np.int64) % ncx
+        gy = (cand[:, 1] / ny * ncy).astype(np.int64) % ncy
+        cy = (gy[:, None, None] + offs[None, :, None]) % ncy
+        cx = (gx[:, None, None] + offs[None, None, :]) % ncx
+        q = slots[cy, cx].reshape(len(cand), -1, 3)
+        dx = np.abs(cand[:, None, 0] - q[..., 0])
+        dx = np.minimum(dx, nx - dx)
+        dy = np.abs(cand[:, None, 1] - q[..., 1])
+        dy = np.minimum(dy, ny - dy)
+        ok = (dx * dx + dy * dy >= (r + q[..., 2] + gap) ** 2).all(axis=1)
+        idx = np.flatnonzero(ok)
+        return int(idx[0]) if idx.size else -1
+
+    def add(x, y, r):
+        gx, gy = int(x / nx * ncx) % ncx, int(y / ny * ncy) % ncy
+        n = count[gy, gx]
+        if n >= K:
+            raise RuntimeError("cell list overflow")
+        slots[gy, gx, n] = (x, y, r)
+        count[gy, gx] = n + 1
+        centres.append((float(x), float(y)))
+        radii.append(float(r))
 
     n_draw = int(target / (math.pi * ((rmin + rmax) / 2) ** 2) * 1.3) + 1
     draws = np.sort(rng.uniform(rmin, rmax, n_draw))[::-1]
     for r in draws:
         if filled >= target:
             break
-        for _ in range(max_tries):
-            cx, cy = rng.uniform(0, nx), rng.uniform(0, ny)
-            if fits(cx, cy, r):
-                add(cx, cy, r)
-                filled += math.pi * r * r
-                break
+        cand = rng.uniform(0.0, 1.0, (max_tries, 2)) * np.array([nx, ny])
+        i = first_fit(cand, r)
+        if i >= 0:
+            add(cand[i, 0], cand[i, 1], r)
+            filled += math.pi * r * r
     misses = 0
     while filled < target and misses < 20 * max_tries:
-        cx, cy = rng.uniform(0, nx), rng.uniform(0, ny)
-        if fits(cx, cy, rmin):
-            add(cx, cy, rmin)
+        cand = rng.uniform(0.0, 1.0, (max_tries, 2)) * np.array([nx, ny])
+        i = first_fit(cand, rmin)
+        if i >= 0:
+            add(cand[i, 0], cand[i, 1], rmin)
             filled += math.pi * rmin * rmin
             misses = 0
         else:
-            misses += 1
+            misses += max_tries
     rho = droplets(nx, ny, centres, radii, seed=seed, noise=noise, periodic=True)
     achieved = float((rho[0] > 0.5).mean())
     return rho, centres, radii, achieved

@@ -83,8 +83,16 @@ def channel_spec(tau_d, tau_b=1.0):
     return dict(nx=NX, ny=NY, tau=(tau_d, tau_b), walls=1, wall_mode=1, wall_rho=(0.03, 1.0), g=(1e-6, 0.0))
 
 
+def channel_emulsion(phi):
+    return W.hex_emulsion(NX, NY, phi, R=12.0, spread=2.0, gap=3.0, walls=True, seed=W.BASE_SEED + 2)
+
+
 def channel_field(phi):
-    return W.hex_emulsion(NX, NY, phi, R=12.0, spread=2.0, gap=3.0, walls=True, seed=W.BASE_SEED + 2)[0]
+    return channel_emulsion(phi)[0]
+
+
+# area fraction each configured one reaches (within 0.01), for the test ids
+PHI_ACHIEVED = {phi: channel_emulsion(phi)[3] for phi in (0.3, 0.5, 0.7)}
 
 
 def run_series(lbmod, precision, specs, fields):
@@ -114,10 +122,13 @@ def channel_runs(lbmod):
     return mu32, mu64
 
 
-@pytest.mark.parametrize("case", range(len(CASES)), ids=["phi%.1f-M%s" % (p, "3" if t > 1 else "1/3") for p, t in CASES])
+@pytest.mark.parametrize("case", range(len(CASES)),
+                         ids=["phi%.1f(%.3f)-M%s" % (p, PHI_ACHIEVED[p], "3" if t > 1 else "1/3") for p, t in CASES])
 def test_channel_emulsion_fp32_vs_fp64_50k_steps(channel_runs, case):
     """1024 x 256 channel, non-wetting walls, g = 1e-6, droplets of radius
-    12 +- 2 on a jittered hexagonal lattice; viscosity ratio mu_d/mu_c = 3
+    12 +- 2 on a jittered hexagonal lattice (clipped to keep the gaps: at 0.7
+    the radii are 10-10.7 with 2.5-node gaps), the id giving the area
+    fraction reached; viscosity ratio mu_d/mu_c = 3
     (tau_d = 2) or 1/3 (tau_d = 2/3); mu_r every 10000 steps up to 50000.
 
     Where mu_r is well conditioned (the FP64 runs at tau_B -+ 1e-5 move it by

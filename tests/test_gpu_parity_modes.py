@@ -1,0 +1,100 @@
+"""2000-step parity with the oracle of every execution mode of the time step,
+on lattices whose tiles are all full tiles staged by the tensor memory
+accelerator in LB_MODE_TMA (sides multiples of 32 x 8, at least 40 x 12):
+
+- a 256 x 128 periodic droplet, R = 30, viscosity ratio 2 (tau_A = 2);
+- a 256 x 96 channel between half-way bounce-back walls with fixed
+  non-wetting ghost densities (0.03, 1.0) and a body force g_x = 1e-6, two
+  drops of radius 14 and 16, viscosity ratio 1/3 (tau_B = 2/3).
+
+Tolerances (normwise, ||x - x_ref||_inf / ||x_ref||_inf per field):
+FP64 populations, densities and barycentric velocities 1e-12; FP32 offset
+populations 1e-5 on densities and velocities (Secs. II A-B: Eqs. 1-3, 5, 6,
+8, 9; half-way bounce-back of Sec. III A; wall ghosts of Sec. III D)."""
+import numpy as np
+import pytest
+
+from paper_1806_06943_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+C6 = dict(G_AB=3.0, G1=-7.4, G2=6.4)
+STEPS = 2000
+
+
+def _cases():
+    return {
+        "droplet_256x128": (lambda: W.droplet(256, 128, 30.0, seed=W.BASE_SEED + 10), dict(tau=(2.0, 1.0), **C6)),
+        "channel_256x96": (lambda: W.droplets(256, 96, [(70.0, 40.0), (190.0, 55.0)], [14.0, 16.0],
+                                              seed=W.BASE_SEED + 11, periodic=False),
+                           dict(tau=(1.0, 2.0 / 3.0), g=(1e-6, 0.0), walls=1, wall_mode=1, wall_rho=(0.03, 1.0), **C6)),
+    }
+
+
+CASES = _cases()
+
+
+@pytest.fixture(scope="module")
+def lbmod():
+    from paper_1806_06943_gb300 import build
+    build.build()
+    from paper_1806_06943_gb300 import lb
+    return lb
+
+
+@pytest.fixture(scope="module")
+def references(oracle_mod):
+    """The oracle's state after STEPS steps, per case (computed once)."""
+    out = {}
+    for name, (field, kw) in CASES.items():
+        rho = field()
+        ny, nx = rho.shape[1:]
+        o = oracle_mod.OracleSim(nx, ny, **kw)
+        o.set_fields(rho)
+        o.step(STEPS)
+        out[name] = (rho, o.fields(), o.get_f(), o.observables())
+    return out
+
+
+def nrel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def run(lbmod, rho, kw, precision, mode, ty):
+    ny, nx = rho.shape[1:]
+    g = lbmod.Lattice(nx, ny, precision=precision, **kw)
+    g.set_config(mode, ty)
+    g.set_fields(rho)
+    g.step(STEPS)
+    return g
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("mode,ty", [("TMA", 8), ("TMA", 4), ("TMA", 2), ("FUSED", 8), ("LAUNCH", 4)])
+def test_fp32_modes_match_the_oracle(lbmod, references, case, mode, ty):
+    rho, fo, _, oo = references[case]
+    g = run(lbmod, rho, CASES[case][1], lbmod.LB_FP32, getattr(lbmod, "LB_MODE_" + mode), ty)
+    fg = g.fields()
+    er, eu = nrel(fg["rho"], fo["rho"]), nrel(fg["ubar"], fo["ubar"])
+    print(f"{case} FP32 {mode} ty={ty}: rho {er:.2e} u {eu:.2e}")
+    assert er <= 1e-5, er
+    assert eu <= 1e-5, eu
+    og = g.observables()
+    for k in ("massA", "massB"):
+        assert abs(og[k] - oo[k]) <= 1e-5 * oo[k], k
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("mode,ty", [("FUSED", 8), ("FUSED", 2), ("PERSISTENT", 4)])
+def test_fp64_modes_match_the_oracle(lbmod, references, case, mode, ty):
+    rho, fo, fpo, oo = references[case]
+    g = run(lbmod, rho, CASES[case][1], lbmod.LB_FP64, getattr(lbmod, "LB_MODE_" + mode), ty)
+    fg = g.fields()
+    assert nrel(fg["rho"], fo["rho"]) <= 1e-12
+    assert nrel(fg["ubar"], fo["ubar"]) <= 1e-12
+    assert nrel(g.get_populations(), fpo) <= 1e-12
+    og = g.observables()
+    for k in ("massA", "massB"):
+        assert abs(og[k] - oo[k]) <= 1e-12 * oo[k], k
+    if CASES[case][1].get("walls"):
+        assert abs(og["mu_r"] - oo["mu_r"]) <= 1e-10 * abs(oo["mu_r"])

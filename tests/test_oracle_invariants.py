@@ -94,3 +94,23 @@ def test_uniform_state_is_steady(oracle_mod):
     fl = s.fields()
     assert np.max(np.abs(fl["ubar"])) < 1e-16
     assert np.max(np.abs(fl["rho"][0] - 0.3)) < 1e-15
+
+
+def test_threaded_oracle_is_bitwise_single_threaded(oracle_mod):
+    """The row loops may run on several OpenMP threads; every node's
+    arithmetic is the same on any thread, so the state is bitwise that of one
+    thread (walls, body force and ragged sizes included)."""
+    rho = W.droplet(45, 37, 9.0, seed=15, periodic=False)
+    kw = dict(tau=(0.7, 1.6), g=(2e-5, 0.0), walls=1, wall_mode=0)
+    runs = []
+    n0 = oracle_mod.set_threads(0)
+    try:
+        for n in (1, 4):
+            oracle_mod.set_threads(n)
+            s = oracle_mod.OracleSim(45, 37, **kw)
+            s.set_fields(rho)
+            s.step(120)
+            runs.append(s.get_f())
+    finally:
+        oracle_mod.set_threads(n0)
+    assert np.array_equal(runs[0], runs[1])
