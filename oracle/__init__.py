@@ -55,6 +55,7 @@ class OrcParams(ctypes.Structure):
         ("g", ctypes.c_double * 2),
         ("walls", ctypes.c_int32), ("wall_mode", ctypes.c_int32),
         ("wall_rho", ctypes.c_double * 2),
+        ("forcing", ctypes.c_int32), ("pad", ctypes.c_int32),
     ]
 
 
@@ -84,6 +85,8 @@ def _load():
             lib.orc_guo.argtypes = [d, d, d, d, d, dp]
             lib.orc_tables.argtypes = [dp, P(ctypes.c_int32), P(ctypes.c_int32), dp,
                                        P(ctypes.c_int32), P(ctypes.c_int32)]
+            lib.orc_shift_forcing.argtypes = [d, d, d, d, d, d, dp]
+            lib.orc_pressure_tensor.argtypes = [ctypes.c_void_p, dp]
             lib.orc_set_threads.restype = ctypes.c_int
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_bulk_pressure.restype = d
@@ -97,8 +100,11 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+FORCING_GUO, FORCING_SHIFT = 0, 1
+
+
 def make_params(nx, ny, tau=(1.0, 1.0), G_AB=3.0, G1=-7.4, G2=6.4, g=(0.0, 0.0),
-                walls=0, wall_mode=0, wall_rho=(0.0, 0.0)) -> OrcParams:
+                walls=0, wall_mode=0, wall_rho=(0.0, 0.0), forcing=FORCING_GUO) -> OrcParams:
     p = OrcParams()
     p.nx, p.ny = int(nx), int(ny)
     p.tau[0], p.tau[1] = float(tau[0]), float(tau[1])
@@ -106,6 +112,7 @@ def make_params(nx, ny, tau=(1.0, 1.0), G_AB=3.0, G1=-7.4, G2=6.4, g=(0.0, 0.0),
     p.g[0], p.g[1] = float(g[0]), float(g[1])
     p.walls, p.wall_mode = int(walls), int(wall_mode)
     p.wall_rho[0], p.wall_rho[1] = float(wall_rho[0]), float(wall_rho[1])
+    p.forcing = int(forcing)
     return p
 
 
@@ -172,6 +179,12 @@ class OracleSim:
         self.lib.orc_fields(self.h, _dptr(rho), _dptr(mom), _dptr(force), _dptr(ueq), _dptr(ubar))
         return {"rho": rho, "mom": mom, "force": force, "ueq": ueq, "ubar": ubar}
 
+    def pressure_tensor(self) -> np.ndarray:
+        """[2][3][ny][nx]: kinetic and interaction parts (Eqs. 10, 13), xx, yy, xy."""
+        out = np.empty((2, 3, self.ny, self.nx))
+        self.lib.orc_pressure_tensor(self.h, _dptr(out))
+        return out
+
     def observables(self, probe=(0.0, 0.0, 0.0)) -> dict:
         out = np.empty(12)
         cx, cy, R = probe
@@ -188,6 +201,12 @@ def equilibrium(rho, ux, uy) -> np.ndarray:
 def guo(tau, ux, uy, Fx, Fy) -> np.ndarray:
     out = np.empty(9)
     _load().orc_guo(float(tau), float(ux), float(uy), float(Fx), float(Fy), _dptr(out))
+    return out
+
+
+def shift_forcing(tau, rho, ux, uy, Fx, Fy) -> np.ndarray:
+    out = np.empty(9)
+    _load().orc_shift_forcing(float(tau), float(rho), float(ux), float(uy), float(Fx), float(Fy), _dptr(out))
     return out
 
 
@@ -210,3 +229,20 @@ def tables() -> dict:
     _load().orc_tables(_dptr(w), ex.ctypes.data_as(I), ey.ctypes.data_as(I), _dptr(p),
                        jx.ctypes.data_as(I), jy.ctypes.data_as(I))
     return {"w": w, "ex": ex, "ey": ey, "p": p, "jx": jx, "jy": jy}
+
+
+def disjoining_pressure(h, s) -> np.ndarray:
+    """Disjoining pressure of Eq. (18), Pi(h) = s(h)/h - int_h^inf s(t)/t^2 dt,
+    from samples s(h_i) = gamma_f(h_i) - 2 gamma (Eq. 17) at increasing h_i:
+    the integral by the trapezoid rule over the samples, s taken as zero
+    beyond the last one (the boundary condition Pi(inf) = 0)."""
+    h = np.asarray(h, dtype=np.float64)
+    s = np.asarray(s, dtype=np.float64)
+    g = s / (h * h)
+    out = np.empty_like(h)
+    for i in range(len(h)):
+        tail = 0.0
+        for j in range(i, len(h) - 1):
+            tail += 0.5 * (g[j] + g[j + 1]) * (h[j + 1] - h[j])
+        out[i] = s[i] / h[i] - tail
+    return out

@@ -88,6 +88,9 @@ typedef struct orc_params {
     int32_t walls;      /* 0: periodic in y; 1: half-way bounce-back at y=-1/2 and y=ny-1/2 */
     int32_t wall_mode;  /* 0: mirrored ghost densities; 1: fixed ghost densities */
     double wall_rho[2]; /* ghost densities for wall_mode 1 */
+    int32_t forcing;    /* 0: Guo forcing, Eqs. (5)-(6), the present model;
+                           1: velocity-shift forcing, Eq. (4), the original model */
+    int32_t pad;
 } orc_params;
 
 typedef struct orc_sim {
@@ -122,6 +125,7 @@ void orc_destroy(orc_sim *s)
 orc_sim *orc_create(const orc_params *p)
 {
     if (p->nx < 5 || p->ny < 5 || !(p->tau[0] > 0.5) || !(p->tau[1] > 0.5)) return NULL;
+    if (p->forcing != 0 && p->forcing != 1) return NULL;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     if (!s) return NULL;
     s->p = *p;
@@ -296,8 +300,42 @@ static void site_moments(const orc_sim *s, int x, int y, double rho[2], double m
     ueq[1] = (om0 * m[0][1] + om1 * m[1][1]) / den;
 }
 
-/* One time step: collide with Guo forcing (Eqs. 1, 2, 5), then stream; a
- * population that would cross a wall returns to its own node reversed
+/* Velocity-shift forcing term of the original model, Eq. (4):
+ * C^SC_i = (1/tau) [f^eq_i(rho, u + F tau / rho) - f^eq_i(rho, u)], u = u^eq. */
+void orc_shift_forcing(double tau, double rho, double ux, double uy, double Fx, double Fy, double C[9])
+{
+    double omega = 1.0 / tau;
+    double feq[9], feqs[9];
+    orc_equilibrium(rho, ux, uy, feq);
+    orc_equilibrium(rho, ux + tau * Fx / rho, uy + tau * Fy / rho, feqs);
+    for (int i = 0; i < 9; ++i) C[i] = omega * (feqs[i] - feq[i]);
+}
+
+/* Common velocity of the original model: Eq. (3) with the component momenta
+ * sum_i f e_i, without the force (Sec. II A, after Eq. 4). */
+static void site_moments_shift(const orc_sim *s, int x, int y, double rho[2], double ueq[2])
+{
+    double m[2][2];
+    for (int k = 0; k < 2; ++k) {
+        double jx = 0.0, jy = 0.0;
+        for (int i = 0; i < 9; ++i) {
+            double fi = s->f[FIDX(s, k, i, x, y)];
+            jx += fi * EX[i];
+            jy += fi * EY[i];
+        }
+        rho[k] = s->rho[RIDX(s, k, x, y)];
+        m[k][0] = jx;
+        m[k][1] = jy;
+    }
+    double om0 = 1.0 / s->p.tau[0], om1 = 1.0 / s->p.tau[1];
+    double den = om0 * rho[0] + om1 * rho[1];
+    ueq[0] = (om0 * m[0][0] + om1 * m[1][0]) / den;
+    ueq[1] = (om0 * m[0][1] + om1 * m[1][1]) / den;
+}
+
+/* One time step: collide with Guo forcing (Eqs. 1, 2, 5), or with the
+ * velocity-shift forcing of the original model (Eqs. 1, 2, 4), then stream;
+ * a population that would cross a wall returns to its own node reversed
  * (half-way bounce-back, Sec. III A). */
 static void step_once(orc_sim *s)
 {
@@ -308,12 +346,15 @@ static void step_once(orc_sim *s)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             double rho[2], m[2][2], ueq[2];
-            site_moments(s, x, y, rho, m, ueq);
+            if (s->p.forcing == 1) site_moments_shift(s, x, y, rho, ueq);
+            else site_moments(s, x, y, rho, m, ueq);
             for (int k = 0; k < 2; ++k) {
                 double omega = 1.0 / s->p.tau[k];
                 double feq[9], C[9];
+                double Fx = s->force[FOIDX(s, k, 0, x, y)], Fy = s->force[FOIDX(s, k, 1, x, y)];
                 orc_equilibrium(rho[k], ueq[0], ueq[1], feq);
-                orc_guo(s->p.tau[k], ueq[0], ueq[1], s->force[FOIDX(s, k, 0, x, y)], s->force[FOIDX(s, k, 1, x, y)], C);
+                if (s->p.forcing == 1) orc_shift_forcing(s->p.tau[k], rho[k], ueq[0], ueq[1], Fx, Fy, C);
+                else orc_guo(s->p.tau[k], ueq[0], ueq[1], Fx, Fy, C);
                 for (int i = 0; i < 9; ++i) {
                     double fi = s->f[FIDX(s, k, i, x, y)];
                     double fpost = fi - omega * (fi - feq[i]) + C[i];
@@ -493,4 +534,62 @@ void orc_observables(orc_sim *s, double cx, double cy, double R, double out[12])
     out[10] = umax;
     out[11] = finite ? 1.0 : 0.0;
     free(rho); free(mom); free(ub);
+}
+
+/* Pressure tensor at the current time, per node (Sec. II B, Eq. 10):
+ *   P_ab = P^kin_ab + P^int_ab
+ *   P^kin_ab = sum_k sum_i f_k,i e_ia e_ib                          Eq. (13)
+ *   P^int_ab = 1/2 sum_k [ G1 psi_k(x) sum_i w_i psi_k(x + e_i) e_ia e_ib
+ *                        + G2 psi_k(x) sum_j p_j psi_k(x + e_j) e_ja e_jb
+ *                        + G_AB rho_k(x) sum_i w_i rho_kbar(x + e_i) e_ia e_ib ]
+ * The paper defines P^int only through its divergence, Eq. (12), and refers
+ * elsewhere for the lattice form.  This is the form that gives each pair of
+ * interacting nodes' contribution half to each node (the force of Eqs. 8-9
+ * is a sum of such pair forces): in a uniform state it is the bulk pressure
+ * of Eq. (11) minus sum_k rho_k cs^2, and summed over the nodes of a profile
+ * it equals the sum of the momentum flux through the planes between the
+ * nodes, whose differences are -sum_k F_k (Eq. 12), so the surface-tension
+ * integral of Eq. (15) does not depend on how the pair contributions are
+ * shared out.  Ghost densities and periodic copies are those of the forces.
+ *   out [2][3][ny][nx]: kinetic then interaction part; components xx, yy, xy */
+void orc_pressure_tensor(orc_sim *s, double *out)
+{
+    int nx = s->p.nx, ny = s->p.ny;
+    size_t n = (size_t)nx * ny;
+    forces(s);    /* densities, ghost rows and psi of the current populations */
+    const double G1 = s->p.G1, G2 = s->p.G2, GAB = s->p.G_AB;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t c = (size_t)y * nx + x;
+            double kin[3] = {0.0, 0.0, 0.0}, pint[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < 2; ++k) {
+                for (int i = 0; i < 9; ++i) {
+                    double fi = s->f[FIDX(s, k, i, x, y)];
+                    kin[0] += fi * EX[i] * EX[i];
+                    kin[1] += fi * EY[i] * EY[i];
+                    kin[2] += fi * EX[i] * EY[i];
+                }
+                int kb = 1 - k;
+                double psi = s->psi_ext[EIDX(s, k, x, y)], rho = s->rho_ext[EIDX(s, k, x, y)];
+                double s1[3] = {0.0, 0.0, 0.0}, s2[3] = {0.0, 0.0, 0.0}, s3[3] = {0.0, 0.0, 0.0};
+                for (int i = 0; i < 9; ++i) {
+                    double w = w_of(EX[i] * EX[i] + EY[i] * EY[i]);
+                    double a = w * s->psi_ext[EIDX(s, k, XW(s, x + EX[i]), y + EY[i])];
+                    double b = w * s->rho_ext[EIDX(s, kb, XW(s, x + EX[i]), y + EY[i])];
+                    s1[0] += a * EX[i] * EX[i]; s1[1] += a * EY[i] * EY[i]; s1[2] += a * EX[i] * EY[i];
+                    s3[0] += b * EX[i] * EX[i]; s3[1] += b * EY[i] * EY[i]; s3[2] += b * EX[i] * EY[i];
+                }
+                for (int j = 0; j < 25; ++j) {
+                    int dx = JX(j), dy = JY(j);
+                    double a = p_of(dx * dx + dy * dy) * s->psi_ext[EIDX(s, k, XW(s, x + dx), y + dy)];
+                    s2[0] += a * dx * dx; s2[1] += a * dy * dy; s2[2] += a * dx * dy;
+                }
+                for (int c3 = 0; c3 < 3; ++c3)
+                    pint[c3] += 0.5 * (G1 * psi * s1[c3] + G2 * psi * s2[c3] + GAB * rho * s3[c3]);
+            }
+            for (int c3 = 0; c3 < 3; ++c3) {
+                out[(size_t)c3 * n + c] = kin[c3];
+                out[(size_t)(3 + c3) * n + c] = pint[c3];
+            }
+        }
 }

@@ -73,3 +73,18 @@ def test_smooth_droplet_profile():
     # next, rho(R) - rho(R + 1) = (hi - lo) tanh(2 / w) / 2
     assert np.interp(R, r[64:], prof[64:]) == pytest.approx(0.5 * (hi + lo), abs=1e-12)
     assert S.interface_width(prof) == pytest.approx(2.0 / np.tanh(2.0 / w), rel=1e-9)
+
+
+def test_disjoining_pressure_quadrature_against_a_closed_form(oracle_mod):
+    """Eq. (18) for s(h) = a (1/h - 1/H) on h <= H (zero beyond):
+    Pi(h) = s/h - a [1/(2h^2) - 1/(2H^2) - (1/h - 1/H)/H], by both the
+    oracle's quadrature and the sweep module's, on a fine grid."""
+    from paper_1806_06943_gb300 import sweeps
+    a, H = 0.3, 40.0
+    h = np.linspace(2.0, H, 4001)
+    s = a * (1.0 / h - 1.0 / H)
+    exact = s / h - a * (0.5 / h ** 2 - 0.5 / H ** 2 - (1.0 / h - 1.0 / H) / H)
+    for Pi in (oracle_mod.disjoining_pressure(h, s), sweeps.disjoining_pressure(h, s)):
+        assert np.max(np.abs(Pi - exact)) <= 3e-5 * np.max(np.abs(exact))   # trapezoid, dh = 0.0095
+    assert np.allclose(oracle_mod.disjoining_pressure(h[::20], s[::20]),
+                       sweeps.disjoining_pressure(h[::20], s[::20]), rtol=0, atol=1e-15)
