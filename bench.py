@@ -55,11 +55,13 @@ FLOOR_BYTES = {1: 144, 0: 288}
 BYTES_FUSED = {1: 160, 0: 288}     # one-pass: 18 pops read + 18 written (+ 2 reference rho read, 2 written)
 BYTES_COLLIDE = {1: 160, 0: 304}   # two-pass fused kernel: 18 pops read + 18 written + 2 rho read (+ 2 reference rho read)
 BYTES_DENSITY = {1: 88, 0: 160}    # density pass: 18 pops read + 2 rho written (+ 2 reference rho read)
-# FP64 operations per node of the FP64 one-pass kernel (k_fused<double, 8>),
-# DADD + DMUL + 2 DFMA thread instructions per node from ncu on the 512^2
-# dense emulsion (profiles/k_fused_fp64_dense_emulsion_512.md); None until
-# measured on the current kernel.
-FP64_FLOPS_PER_NODE = None
+# FP64 operations per node of the FP64 one-pass kernel (k_fused<double, 8>):
+# DADD + DMUL + 2 DFMA thread instructions per node (344 + 236 + 2 x 61.25),
+# counted by ncu on the 512^2 dense emulsion
+# (profiles/k_fused_fp64_dense_emulsion_512.md); FP64 pipe instructions per
+# node (DADD + DMUL + DFMA) beside it.
+FP64_FLOPS_PER_NODE = 702.6
+FP64_PIPE_OPS_PER_NODE = 641.3
 
 
 def parse():
@@ -262,6 +264,7 @@ def alu_roofline(kname, units, ms, peak_tflops, hbm_peak):
             "frac": (ach / peak_tflops) if (ach and peak_tflops) else None, "traffic": None,
             "peak_source": "measured FP64 FMA throughput of this device (lb_device_fp64_peak)",
             "flops_per_site": FP64_FLOPS_PER_NODE, "units_per_launch": units, "ms_per_launch": ms,
+            "fp64_pipe_frac": FP64_PIPE_OPS_PER_NODE * units / (ms * 1e-3) / (peak_tflops * 1e12 / 2),
             "hbm_frac_floor": FLOOR_BYTES[0] * units / (ms * 1e-3) / 1e9 / hbm_peak}
 
 

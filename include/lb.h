@@ -86,6 +86,20 @@ extern "C" {
 #define LB_MODE_FUSED 2
 #define LB_MODE_TMA 3
 
+/* How the force enters the collision (lb_params.forcing).
+ * LB_FORCING_GUO: the method of the paper: Guo forcing term of Eq. (5),
+ *   component momenta with half the force (Eq. 6) in u^eq of Eq. (3).
+ * LB_FORCING_SHIFT: the original two-range model the paper compares with:
+ *   u^eq of Eq. (3) from the momenta sum_i f e_i without force, and the
+ *   velocity-shift forcing term of Eq. (4), i.e. species k relaxes to
+ *   f^eq(rho_k, u^eq + tau_k F_k / rho_k), which needs rho_k > 0 at every
+ *   node (a vanishing species makes the shift non-finite, reported as
+ *   LB_EUNSTABLE by the observables).  LB_FP64 populations only; no adjoint
+ *   (lb_grad) for it.  The observables and fields keep the
+ *   half-force momenta of Eq. (6) in both forms. */
+#define LB_FORCING_GUO 0
+#define LB_FORCING_SHIFT 1
+
 /* Densities the interaction stencils see beyond a wall (ghost rows
  * y = -1, -2 and y = ny, ny + 1). */
 #define LB_WALL_MIRROR 0  /* row -1 <- row 0, row -2 <- row 1, and symmetrically at the top */
@@ -102,6 +116,8 @@ extern "C" {
  *   wall_mode  LB_WALL_MIRROR or LB_WALL_FIXED (ignored without walls)
  *   wall_rho   ghost densities for LB_WALL_FIXED
  *   precision  LB_FP64 or LB_FP32
+ *   forcing    LB_FORCING_GUO (the method) or LB_FORCING_SHIFT (the original
+ *              model's velocity shift, LB_FP64 only)
  *   stream     the cudaStream_t to run on (see above), or NULL */
 typedef struct lb_params {
     int32_t nx, ny;
@@ -112,7 +128,7 @@ typedef struct lb_params {
     int32_t wall_mode;
     double wall_rho[2];
     int32_t precision;
-    int32_t reserved;
+    int32_t forcing;
     void *stream;
 } lb_params;
 
@@ -215,6 +231,25 @@ int lb_observables(lb_handle *h, lb_obs *o);
  * Synchronises. */
 int lb_get_fields(lb_handle *h, double *rho, double *mom, double *ubar);
 
+/* Pressure tensor at the current time (Sec. II B, Eq. 10), in FP64, from the
+ * pre-collision populations and the densities they give:
+ *   kinetic part      P^kin_ab = sum_k sum_i f_k,i e_ia e_ib             Eq. (13)
+ *   interaction part  P^int_ab = 1/2 sum_k [G1 psi_k(x) sum_i w_i psi_k(x + e_i) e_ia e_ib
+ *                                + G2 psi_k(x) sum_j p_j psi_k(x + e_j) e_ja e_jb
+ *                                + G_AB rho_k(x) sum_i w_i rho_kbar(x + e_i) e_ia e_ib]
+ * The paper defines P^int by its divergence (Eq. 12) only; this per-node form
+ * shares each pair interaction of Eqs. (8), (9) equally between its two
+ * nodes: uniform states give the bulk pressure of Eq. (11), and the sum over
+ * a flat interface, which the surface tension of Eq. (15) integrates, equals
+ * that of any other sharing.  Ghost rows and periodic copies are those of
+ * the forces.
+ *   P     host [2][3][ny][nx] (kinetic, interaction; components xx, yy, xy),
+ *         or NULL
+ *   sums  host [6]: the lattice sums of the six fields (same order), or NULL
+ * For a flat interface normal to x in a periodic lattice (two interfaces),
+ * gamma = (sums[0] + sums[3] - sums[1] - sums[4]) / (2 ny).  Synchronises. */
+int lb_pressure_tensor(lb_handle *h, double *P, double sums[6]);
+
 /* Copy the populations f_k,i (as FP64; for LB_FP32 with w_i R added back) to
  * host [2][9][ny][nx], direction order: rest, (1,0), (0,1), (-1,0), (0,-1),
  * (1,1), (-1,1), (-1,-1), (1,-1).  Synchronises. */
@@ -283,6 +318,9 @@ int lb_batch_set_probe(lb_batch *b, int32_t i, double cx, double cy, double R);
 /* o points to n lb_obs, one per lattice.  Synchronises. */
 int lb_batch_observables(lb_batch *b, lb_obs *o);
 int lb_batch_get_fields(lb_batch *b, int32_t i, double *rho, double *mom, double *ubar);
+/* As lb_pressure_tensor, for lattice i of the batch (the sums of every
+ * lattice are formed by one launch). */
+int lb_batch_pressure_tensor(lb_batch *b, int32_t i, double *P, double sums[6]);
 /* As lb_profile, over all lattices of the batch (one launch covers them all). */
 int lb_batch_profile(lb_batch *b, int32_t nsteps, void *flush_buf, size_t flush_bytes, double ms[3]);
 /* As lb_set_config, lb_get_config and lb_autotune, for the whole batch. */

@@ -75,6 +75,10 @@ int validate(const lb_params *p, int i)
     if (p->walls != LB_PERIODIC && p->walls != LB_WALLS_Y) return fail(LB_EINVAL, "walls must be 0 or 1");
     if (p->wall_mode != LB_WALL_MIRROR && p->wall_mode != LB_WALL_FIXED) return fail(LB_EINVAL, "wall_mode must be 0 or 1");
     if (p->precision != LB_FP64 && p->precision != LB_FP32) return fail(LB_EINVAL, "precision must be LB_FP64 or LB_FP32");
+    if (p->forcing != LB_FORCING_GUO && p->forcing != LB_FORCING_SHIFT)
+        return fail(LB_EINVAL, "forcing must be LB_FORCING_GUO or LB_FORCING_SHIFT");
+    if (p->forcing == LB_FORCING_SHIFT && p->precision != LB_FP64)
+        return fail(LB_EINVAL, "forcing LB_FORCING_SHIFT is built for LB_FP64 populations only");
     return LB_OK;
 }
 
@@ -88,10 +92,12 @@ void fill_lat(lbk::Lat<real> &L, const lb_params &p)
     L.plane = (size_t)L.pitch * p.ny;
     L.walls = p.walls;
     L.wall_mode = p.wall_mode;
+    L.forcing = p.forcing;
     const double wcls[3] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0};
     for (int k = 0; k < 2; ++k) {
         const double omega = 1.0 / p.tau[k];
         L.omega[k] = (real)omega;
+        L.tau[k] = (real)p.tau[k];
         for (int c = 0; c < 3; ++c) L.aw[k][c] = (real)((1.0 - 0.5 * omega) * wcls[c]);
         L.g[k] = (real)p.g[k];
         L.wall_rho[k] = (real)p.wall_rho[k];
@@ -166,6 +172,7 @@ struct lb_engine {
     std::string tma_why = "LB_MODE_TMA needs LB_FP32 populations";
     double *d_partials = nullptr;
     double *d_obs = nullptr;
+    double *d_psum = nullptr;         // pressure-tensor sums, kPStride doubles per lattice
     double *d_tmp = nullptr;
     size_t tmp_elems = 0;
     int64_t t = 0;
@@ -189,6 +196,7 @@ struct lb_engine {
         cudaFree(d_tmaps);
         cudaFree(d_partials);
         cudaFree(d_obs);
+        cudaFree(d_psum);
         cudaFree(d_tmp);
         if (stream && own_stream) cudaStreamDestroy(stream);
     }
@@ -643,6 +651,7 @@ struct lb_engine {
     int grad(int64_t nsteps, int ckpt, int objective, double *J, double dJ[5])
     {
         if (nsteps < 1 || ckpt < 1) return fail(LB_EINVAL, "lb_grad needs nsteps >= 1 and ckpt_every >= 1");
+        if (P[0].forcing != LB_FORCING_GUO) return fail(LB_EINVAL, "lb_grad is the adjoint of the Guo-forcing step only");
         if (!J || !dJ) return fail(LB_EINVAL, "J and dJ must not be NULL");
         const bool f32 = precision == LB_FP32;
         const lb_params &p = P[0];
@@ -826,6 +835,47 @@ struct lb_engine {
         if (rc) return rc;
         if (!all_finite) return fail(LB_EUNSTABLE, "a density or velocity is not finite");
         return LB_OK;
+    }
+
+    // Pressure tensor at the current time (k_pressure): the lattice sums of
+    // its six components for lattice l into sums[6] and, when P is given, the
+    // dense per-node field of lattice l into P [2][3][ny][nx]; host memory.
+    int pressure(int l, double *P, double *sums)
+    {
+        int rc = begin();
+        if (rc) return rc;
+        if ((rc = check_timeout())) return rc;
+        if (!d_psum && cudaMalloc((void **)&d_psum, (size_t)n * lbk::kPStride * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            d_psum = nullptr;
+            return fail(LB_ENOMEM, "cudaMalloc of the pressure-tensor sums failed");
+        }
+        const int nt = (int)tiles.size();
+        const size_t cells = (size_t)nx(l) * ny(l);
+        if (P && (rc = ensure_tmp(6 * cells))) return rc;
+        LB_CUDA(launch_density_obs(parity, 0, nt));
+        if (precision == LB_FP64) {
+            const lbk::Lat<double> *L = (const lbk::Lat<double> *)d_lats;
+            LB_CUDA(lbk::Launch<double>::pressure(L, d_tiles, 0, nt, parity, d_partials, nullptr, stream));
+            LB_CUDA(lbk::Launch<double>::pressure_sum(L, n, d_partials, d_psum, stream));
+            if (P)
+                LB_CUDA(lbk::Launch<double>::pressure(L, d_tiles, tile_begin(l), tile_end(l) - tile_begin(l), parity,
+                                                      nullptr, d_tmp, stream));
+        } else {
+            const lbk::Lat<float> *L = (const lbk::Lat<float> *)d_lats;
+            LB_CUDA(lbk::Launch<float>::pressure(L, d_tiles, 0, nt, parity, d_partials, nullptr, stream));
+            LB_CUDA(lbk::Launch<float>::pressure_sum(L, n, d_partials, d_psum, stream));
+            if (P)
+                LB_CUDA(lbk::Launch<float>::pressure(L, d_tiles, tile_begin(l), tile_end(l) - tile_begin(l), parity,
+                                                     nullptr, d_tmp, stream));
+        }
+        double h[lbk::kPStride];
+        LB_CUDA(cudaMemcpyAsync(h, d_psum + (size_t)l * lbk::kPStride, sizeof h, cudaMemcpyDeviceToHost, stream));
+        if (P) LB_CUDA(cudaMemcpyAsync(P, d_tmp, 6 * cells * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        LB_CUDA(cudaStreamSynchronize(stream));
+        if (sums)
+            for (int a = 0; a < lbk::kNumPSlots; ++a) sums[a] = h[a];
+        return end();
     }
 
     int get_fields(int l, double *rho, double *mom, double *ubar)
@@ -1191,6 +1241,12 @@ int lb_get_fields(lb_handle *h, double *rho, double *mom, double *ubar)
     return h->e->get_fields(0, rho, mom, ubar);
 }
 
+int lb_pressure_tensor(lb_handle *h, double *P, double sums[6])
+{
+    CHECK_H(h);
+    return h->e->pressure(0, P, sums);
+}
+
 int lb_get_populations(lb_handle *h, double *f)
 {
     CHECK_H(h);
@@ -1372,6 +1428,12 @@ int lb_batch_get_fields(lb_batch *b, int32_t i, double *rho, double *mom, double
 {
     CHECK_B(b, i);
     return b->e->get_fields(i, rho, mom, ubar);
+}
+
+int lb_batch_pressure_tensor(lb_batch *b, int32_t i, double *P, double sums[6])
+{
+    CHECK_B(b, i);
+    return b->e->pressure(i, P, sums);
 }
 
 int lb_batch_profile(lb_batch *b, int32_t nsteps, void *flush_buf, size_t flush_bytes, double ms[3])

@@ -552,6 +552,70 @@ __device__ __forceinline__ void node_moments(const real *__restrict__ box, int b
     }
 }
 
+// ---- velocity-shift forcing of the original model (FP64 only) ---------------
+
+// Second-order equilibrium of direction I (Eq. 2), the same expression as
+// collide_dir's.
+template <typename real, int I>
+__device__ __forceinline__ real feq_dir(real rho, real ux, real uy, real uu)
+{
+    constexpr int EX = ex9(I), EY = ey9(I);
+    const real eu = edot<real, EX, EY>(ux, uy);
+    return (real)w9(I) * rho * ((real)1 + (real)3 * eu + (real)4.5 * eu * eu - (real)1.5 * uu);
+}
+
+// BGK relaxation to f^eq(rho, u^eq) plus the velocity-shift term of Eq. (4),
+// C = (1/tau) [f^eq(rho, u^eq + tau F / rho) - f^eq(rho, u^eq)], then the
+// push of direction I of species k.
+template <typename real, int I, bool kInner, class Stage>
+__device__ __forceinline__ void shift_push_dir(const Lat<real> &L, real *__restrict__ fn, const Stage &sg, int k,
+                                               real f, real rho, real ux, real uy, real uu, real sx, real sy, real ss,
+                                               int x, int y, int cx, int cy)
+{
+    const real om = L.omega[k];
+    const real feq = feq_dir<real, I>(rho, ux, uy, uu);
+    const real feqs = feq_dir<real, I>(rho, sx, sy, ss);
+    const real C = om * (feqs - feq);
+    push_dir<real, I, kInner>(L, fn, sg, k, x, y, cx, cy, f - om * (f - feq) + C);
+}
+
+// The node's collision and pushes in the original model: u^eq of Eq. (3)
+// from the momenta sum_i f e_i (no force), species k relaxed with the
+// velocity-shift term of Eq. (4).
+template <typename real, bool kInner, class Stage>
+__device__ __forceinline__ void shift_collide_site(const Lat<real> &L, real *__restrict__ fn, const Stage &sg,
+                                                   real (&fk)[2][9], int x, int y, int cx, int cy)
+{
+    real F[2][2], rho[2], m[2][2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        sg.force(L, k, cx, cy, F[k][0], F[k][1]);
+        rho[k] = sg.density(k, cy, cx);
+        first_moment<real>(fk[k], m[k][0], m[k][1]);
+    }
+    const real om0 = L.omega[0], om1 = L.omega[1];
+    const real den = om0 * rho[0] + om1 * rho[1];
+    const real ux = (om0 * m[0][0] + om1 * m[1][0]) / den;
+    const real uy = (om0 * m[0][1] + om1 * m[1][1]) / den;
+    const real uu = ux * ux + uy * uy;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const real sx = ux + L.tau[k] * F[k][0] / rho[k], sy = uy + L.tau[k] * F[k][1] / rho[k];
+        const real ss = sx * sx + sy * sy;
+        const real(&f)[9] = fk[k];
+        const real r = rho[k];
+        shift_push_dir<real, 0, kInner>(L, fn, sg, k, f[0], r, ux, uy, uu, sx, sy, ss, x, y, cx, cy);
+        shift_push_dir<real, 1, kInner>(L, fn, sg, k, f[1], r, ux, uy, uu, sx, sy, ss, x, y, cx, cy);
+        shift_push_dir<real, 2, kInner>(L, fn, sg, k, f[2], r, ux, uy, uu, sx, sy, ss, x, y, cx, cy);
+        shift_push_dir<real, 3, kInner>(L, fn, sg, k, f[3], r, ux, uy, uu, sx, sy, ss, x, y, cx, cy);
+        shift_push_dir<real, 4, kInner>(L, fn, sg, k, f[4], r, ux, uy, uu, sx, sy, ss, x, y, cx, cy);
+        shift_push_dir<real, 5, kInner>(L, fn, sg, k, f[5], r, ux, uy, uu, sx, sy, ss, x, y, cx, cy);
+        shift_push_dir<real, 6, kInner>(L, fn, sg, k, f[6], r, ux, uy, uu, sx, sy, ss, x, y, cx, cy);
+        shift_push_dir<real, 7, kInner>(L, fn, sg, k, f[7], r, ux, uy, uu, sx, sy, ss, x, y, cx, cy);
+        shift_push_dir<real, 8, kInner>(L, fn, sg, k, f[8], r, ux, uy, uu, sx, sy, ss, x, y, cx, cy);
+    }
+}
+
 // Force, moments, u^eq, collision and push of the node (x, y), staged at
 // (cx, cy).  Its populations are fk (updated in place), or with kBox (FP32)
 // the shared-memory box: box[(k * 9 + i) * box_plane] is population i of
@@ -564,6 +628,12 @@ __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restric
                                              const real *__restrict__ box, int box_plane, const NodeMoments<real> *pre)
 {
     static_assert(!kBox || kOffset<real>, "the box form is FP32 only");
+    if constexpr (!kOffset<real>) {
+        if (L.forcing == 1) {   // the original model (Eq. 4), a block-uniform branch
+            shift_collide_site<real, kInner>(L, fn, sg, fk, x, y, cx, cy);
+            return;
+        }
+    }
     real F[2][2], rho[2], m[2][2], dg[2] = {(real)0, (real)0}, delta[2] = {(real)0, (real)0};
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -1033,6 +1103,143 @@ __global__ void __launch_bounds__(256) k_finalize(const Lat<real> *__restrict__ 
     }
     o[oUmax] = s[kUmax];
     o[oFinite] = s[kNonFinite] == 0.0 ? 1.0 : 0.0;
+}
+
+// ---- pressure tensor (Sec. II B-C) --------------------------------------------
+
+// Slots of the pressure-tensor partial sums, per tile and per lattice.
+enum PSlot { pKinXX = 0, pKinYY, pKinXY, pIntXX, pIntYY, pIntXY, kNumPSlots };
+constexpr int kPStride = 8;
+
+// Second moments sum_i w_i s(x + e_i) e_ia e_ib of a staged plane over the
+// D2Q9 neighbours (xx, yy, xy), in FP64.
+template <typename real>
+__device__ __forceinline__ void q9_second(const real (*s)[SW], int cx, int cy, double (&m)[3])
+{
+    const double W1 = 1.0 / 9.0, W2 = 1.0 / 36.0;
+    const double e = s[cy][cx + 1], w = s[cy][cx - 1], n = s[cy + 1][cx], so = s[cy - 1][cx];
+    const double ne = s[cy + 1][cx + 1], nw = s[cy + 1][cx - 1], sw = s[cy - 1][cx - 1], se = s[cy - 1][cx + 1];
+    const double diag = (ne + nw) + (sw + se);
+    m[0] = W1 * (e + w) + W2 * diag;
+    m[1] = W1 * (n + so) + W2 * diag;
+    m[2] = W2 * ((ne + sw) - (nw + se));
+}
+
+// The same over the D2Q25 neighbours with the weights p(|e|^2).
+template <typename real>
+__device__ __forceinline__ void q25_second(const real (*s)[SW], int cx, int cy, double (&m)[3])
+{
+    m[0] = m[1] = m[2] = 0.0;
+#pragma unroll
+    for (int j = 0; j < 25; ++j) {
+        const int dx = j % 5 - 2, dy = j / 5 - 2;
+        if (dx == 0 && dy == 0) continue;
+        const double a = p25(dx * dx + dy * dy) * (double)s[cy + dy][cx + dx];
+        m[0] += a * (double)(dx * dx);
+        m[1] += a * (double)(dy * dy);
+        m[2] += a * (double)(dx * dy);
+    }
+}
+
+// Per node, in FP64: the kinetic pressure tensor sum_k sum_i f e_a e_b of the
+// pre-collision populations (Eq. 13) and the interaction tensor
+//   P^int_ab = 1/2 sum_k [G1 psi_k S1_ab + G2 psi_k S2_ab + G_AB rho_k S3_ab],
+// S1, S2 the D2Q9 and D2Q25 second moments of psi_k and S3 the D2Q9 second
+// moment of the other species' density: each pair interaction of Eqs. (8),
+// (9) shared equally by its two nodes, which gives the bulk pressure of
+// Eq. (11) in a uniform state and satisfies Eq. (12) summed across a flat
+// interface.  Reduced per tile into FP64 partials (slots PSlot); optionally
+// also written as dense fields out[2][3][ny][nx] (kinetic, interaction; xx,
+// yy, xy).  Reads the density copy parity^1 written by a density pass at the
+// same time.
+template <typename real>
+__global__ void __launch_bounds__(kThreads) k_pressure(const Lat<real> *__restrict__ lats, const int4 *__restrict__ tiles,
+                                                       int tile_offset, int parity, double *__restrict__ partials,
+                                                       double *__restrict__ out)
+{
+    __shared__ real srho[2][SH][SW];
+    __shared__ real spsi[2][SH][SW];
+    __shared__ double sacc[kThreads / 32][kPStride];
+    const int4 t = tiles[tile_offset + blockIdx.x];
+    const Lat<real> &L = lats[t.x];
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    stage_tile<real, SH>(L, L.rho[parity ^ 1], t.y, t.z, srho, spsi, tid, kThreads);
+    __syncthreads();
+    const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
+    double acc[kNumPSlots];
+#pragma unroll
+    for (int a = 0; a < kNumPSlots; ++a) acc[a] = 0.0;
+    if (x < L.nx && y < L.ny) {
+        const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
+        const real *__restrict__ fc = L.f[parity];
+        const size_t c = (size_t)y * L.pitch + x;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const double R = kOffset<real> ? (double)L.rho[parity][(size_t)k * L.plane + c] : 0.0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const double fi = (double)fc[(size_t)(k * 9 + i) * L.plane + c] + w9(i) * R;
+                acc[pKinXX] += fi * (double)(ex9(i) * ex9(i));
+                acc[pKinYY] += fi * (double)(ey9(i) * ey9(i));
+                acc[pKinXY] += fi * (double)(ex9(i) * ey9(i));
+            }
+            double s1[3], s2[3], s3[3];
+            q9_second<real>(spsi[k], cx, cy, s1);
+            q25_second<real>(spsi[k], cx, cy, s2);
+            q9_second<real>(srho[1 - k], cx, cy, s3);
+            const double psi = spsi[k][cy][cx], rho = srho[k][cy][cx];
+            const double G1 = L.G1, G2 = L.G2, GAB = L.GAB;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[pIntXX + a] += 0.5 * (G1 * psi * s1[a] + G2 * psi * s2[a] + GAB * rho * s3[a]);
+        }
+        if (out) {
+            const size_t n = (size_t)L.nx * L.ny, d = (size_t)y * L.nx + x;
+#pragma unroll
+            for (int a = 0; a < kNumPSlots; ++a) out[(size_t)a * n + d] = acc[a];
+        }
+    }
+    if (!partials) return;
+    const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int a = 0; a < kNumPSlots; ++a) {
+        const double v = warp_sum(acc[a]);
+        if (lane == 0) sacc[warp][a] = v;
+    }
+    __syncthreads();
+    if (tid < kNumPSlots) {
+        double v = sacc[0][tid];
+        for (int w = 1; w < kThreads / 32; ++w) v += sacc[w][tid];
+        partials[(size_t)(tile_offset + blockIdx.x) * kPStride + tid] = v;
+    }
+}
+
+// One block per lattice: the pressure-tensor partials of its tiles summed in
+// a fixed order into out[lattice * kPStride + slot].
+template <typename real>
+__global__ void __launch_bounds__(256) k_pressure_sum(const Lat<real> *__restrict__ lats,
+                                                      const double *__restrict__ partials, double *__restrict__ out)
+{
+    __shared__ double sred[256 / 32][kPStride];
+    const Lat<real> &L = lats[blockIdx.x];
+    const int tid = threadIdx.x;
+    double acc[kNumPSlots];
+#pragma unroll
+    for (int a = 0; a < kNumPSlots; ++a) acc[a] = 0.0;
+    for (int tl = L.tile_begin + tid; tl < L.tile_end; tl += 256)
+#pragma unroll
+        for (int a = 0; a < kNumPSlots; ++a) acc[a] += partials[(size_t)tl * kPStride + a];
+    const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int a = 0; a < kNumPSlots; ++a) {
+        const double v = warp_sum(acc[a]);
+        if (lane == 0) sred[warp][a] = v;
+    }
+    __syncthreads();
+    if (tid < kNumPSlots) {
+        double v = sred[0][tid];
+        for (int w = 1; w < 8; ++w) v += sred[w][tid];
+        out[(size_t)blockIdx.x * kPStride + tid] = v;
+    }
 }
 
 // ---- initialisation and population transfer ---------------------------------

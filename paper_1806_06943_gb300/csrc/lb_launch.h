@@ -33,6 +33,12 @@ struct Launch {
     static cudaError_t observe(const Lat<real> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
                                double *partials, double *rho, double *mom, double *ubar, cudaStream_t s);
     static cudaError_t finalize(const Lat<real> *lats, int n_lat, const double *partials, double *obs, cudaStream_t s);
+    // pressure tensor per node of tiles [tile_offset, tile_offset + n_tiles)
+    // of height 4 (partials: 8 doubles per tile; out: dense [6][ny][nx] of
+    // one lattice, or NULL), and its per-lattice sums (8 doubles per lattice)
+    static cudaError_t pressure(const Lat<real> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
+                                double *partials, double *out, cudaStream_t s);
+    static cudaError_t pressure_sum(const Lat<real> *lats, int n_lat, const double *partials, double *out, cudaStream_t s);
     // one lattice, dense FP64 host-layout buffers in device memory
     static cudaError_t init(const Lat<real> *lats, int lat, int nx, int ny, const double *rho, const double *u,
                             int parity, cudaStream_t s);

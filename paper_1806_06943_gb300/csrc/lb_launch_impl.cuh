@@ -108,6 +108,24 @@ cudaError_t Launch<real>::finalize(const Lat<real> *lats, int n_lat, const doubl
 }
 
 template <typename real>
+cudaError_t Launch<real>::pressure(const Lat<real> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
+                                   double *partials, double *out, cudaStream_t s)
+{
+    if (n_tiles <= 0) return cudaSuccess;
+    k_pressure<real><<<n_tiles, dim3(TX, TY), 0, s>>>(lats, tiles, tile_offset, parity, partials, out);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t Launch<real>::pressure_sum(const Lat<real> *lats, int n_lat, const double *partials, double *out,
+                                       cudaStream_t s)
+{
+    if (n_lat <= 0) return cudaSuccess;
+    k_pressure_sum<real><<<n_lat, 256, 0, s>>>(lats, partials, out);
+    return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t Launch<real>::init(const Lat<real> *lats, int lat, int nx, int ny, const double *rho, const double *u,
                                int parity, cudaStream_t s)
 {

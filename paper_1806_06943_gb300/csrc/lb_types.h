@@ -42,8 +42,10 @@ struct Lat {
     int32_t wall_mode;   // 0 mirror, 1 fixed ghost densities
     int32_t tile_begin, tile_end;
     int32_t has_probe;
+    int32_t forcing;     // 0 Guo forcing (Eqs. 5, 6), 1 velocity shift (Eq. 4; FP64 only)
     // model parameters in the compute precision
     real omega[2];       // 1 / tau_k
+    real tau[2];         // tau_k (the velocity shift tau_k F_k / rho_k of Eq. 4)
     real aw[2][3];       // (1 - omega_k / 2) * w(|e|^2) for |e|^2 = 0, 1, 2
     real G1, G2, GAB;
     real g[2];

@@ -26,6 +26,7 @@ LB_WALL_MIRROR, LB_WALL_FIXED = 0, 1
 LB_STATIC_MAX_TILES = 32768
 LB_MODE_LAUNCH, LB_MODE_PERSISTENT, LB_MODE_FUSED, LB_MODE_TMA = 0, 1, 2, 3
 LB_OBJ_MU_R, LB_OBJ_DP = 0, 1
+LB_FORCING_GUO, LB_FORCING_SHIFT = 0, 1
 
 
 class LBError(RuntimeError):
@@ -42,7 +43,7 @@ class lb_params(ctypes.Structure):
         ("g", ctypes.c_double * 2),
         ("walls", ctypes.c_int32), ("wall_mode", ctypes.c_int32),
         ("wall_rho", ctypes.c_double * 2),
-        ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("forcing", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -111,6 +112,8 @@ SIGNATURES = {
     "lb_batch_set_wait_limit": (ctypes.c_int, [_vp, _d, _i32]),
     "lb_observables_static": (ctypes.c_int, [_P(lb_params), _vp, _d, _d, _d, _vp]),
     "lb_device_fp64_peak": (ctypes.c_int, [_i32, _dp]),
+    "lb_pressure_tensor": (ctypes.c_int, [_vp, _vp, _vp]),
+    "lb_batch_pressure_tensor": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
 }
 
 
@@ -160,7 +163,7 @@ def _host_ptr(a: np.ndarray | None, shape, writable=False):
 
 
 def make_params(nx, ny, tau=(1.0, 1.0), G_AB=3.0, G1=-7.4, G2=6.4, g=(0.0, 0.0), walls=0, wall_mode=0,
-                wall_rho=(0.0, 0.0), precision=LB_FP64, stream=None) -> lb_params:
+                wall_rho=(0.0, 0.0), precision=LB_FP64, stream=None, forcing=LB_FORCING_GUO) -> lb_params:
     p = lb_params()
     p.nx, p.ny = int(nx), int(ny)
     p.tau[0], p.tau[1] = float(tau[0]), float(tau[1])
@@ -169,6 +172,7 @@ def make_params(nx, ny, tau=(1.0, 1.0), G_AB=3.0, G1=-7.4, G2=6.4, g=(0.0, 0.0),
     p.walls, p.wall_mode = int(walls), int(wall_mode)
     p.wall_rho[0], p.wall_rho[1] = float(wall_rho[0]), float(wall_rho[1])
     p.precision = int(precision)
+    p.forcing = int(forcing)
     p.stream = stream
     return p
 
@@ -248,6 +252,14 @@ class Lattice:
         _check(LIB.lb_get_fields(self.h, rho.ctypes.data, mom.ctypes.data, ubar.ctypes.data))
         return {"rho": rho, "mom": mom, "ubar": ubar}
 
+    def pressure_tensor(self, field: bool = False):
+        """(sums[6], P or None): lattice sums of the kinetic and interaction
+        xx, yy, xy components, and optionally the field [2][3][ny][nx]."""
+        sums = np.empty(6)
+        P = np.empty((2, 3, self.ny, self.nx)) if field else None
+        _check(LIB.lb_pressure_tensor(self.h, P.ctypes.data if field else None, sums.ctypes.data))
+        return sums, P
+
     def get_populations(self) -> np.ndarray:
         f = np.empty((2, 9, self.ny, self.nx))
         _check(LIB.lb_get_populations(self.h, f.ctypes.data))
@@ -304,7 +316,8 @@ class Batch:
         for i, s in enumerate(specs):
             kw = dict(common)
             kw.update({k: v for k, v in s.items() if k in (
-                "tau", "G_AB", "G1", "G2", "g", "walls", "wall_mode", "wall_rho", "precision", "stream")})
+                "tau", "G_AB", "G1", "G2", "g", "walls", "wall_mode", "wall_rho", "precision", "stream",
+                "forcing")})
             arr[i] = make_params(s["nx"], s["ny"], **kw)
             self.shapes.append((int(s["ny"]), int(s["nx"])))
         self.params = arr
@@ -365,6 +378,13 @@ class Batch:
 
     def set_wait_limit(self, seconds: float, drop_tile: int = -1):
         _check(LIB.lb_batch_set_wait_limit(self.b, float(seconds), int(drop_tile)))
+
+    def pressure_tensor(self, i, field: bool = False):
+        """As Lattice.pressure_tensor, for lattice i."""
+        sums = np.empty(6)
+        P = np.empty((2, 3) + self.shapes[i]) if field else None
+        _check(LIB.lb_batch_pressure_tensor(self.b, int(i), P.ctypes.data if field else None, sums.ctypes.data))
+        return sums, P
 
     def fields(self, i) -> dict:
         n = self.shapes[i]

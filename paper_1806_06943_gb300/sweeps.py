@@ -14,6 +14,12 @@ many lattices per batch.
   F_b = g L^3 rho_B^2 / (8 mu_B^2) and the viscosity ratio M = mu_B / mu_A,
   and the fit of Eq. (20), mu_r = (1 - Phi)^-[eta] (K = 1), with [eta]
   compared against the Taylor and Douglas limits quoted there.
+* Surface tension and disjoining pressure (Secs. II C, III C, Fig. 3): flat
+  interfaces and flat films of B between A regions, periodic in x, the
+  pressure tensor summed over the lattice by the library's reduction kernel:
+  gamma by the integral of Eq. (15), the film tension gamma_f(h) of Eq. (16)
+  and the disjoining pressure Pi(h) of Eq. (18); for either forcing of the
+  collision (Guo, the method; the velocity shift of the original model).
 
 Every time step runs in the library's kernels (FP32 offset form unless asked
 otherwise); this module builds the seeded inputs, reads observables and
@@ -244,3 +250,88 @@ def eta_limits(M: float) -> tuple[float, float]:
     taylor = (1.0 / lam + ETA_INF) / (1.0 / lam + 1.0)
     douglas = (1.0 - 1.0 / lam) / ((1.0 - 1.0 / lam) / ETA_INF + 1.0 / lam)
     return douglas, taylor
+
+
+# ---- surface tension and disjoining pressure (Secs. II C, III C) ---------------
+
+FILM_NY = 5      # rows of a flat-interface lattice: the profile varies along x only
+
+
+def tension_of(sums, ny: int, interfaces: int = 2) -> float:
+    """Eq. (15) from the lattice sums of the pressure tensor (kinetic +
+    interaction, xx minus yy), per unit length of each of the `interfaces`
+    flat interfaces normal to x."""
+    pxx = sums[0] + sums[3]
+    pyy = sums[1] + sums[4]
+    return float(pxx - pyy) / ny / interfaces
+
+
+def coexistence(G1: float, G2: float, G_AB: float, steps: int = 8000, precision: int = lb.LB_FP64):
+    """Bulk densities (majority, minority) of a flat interface equilibrated in
+    a 64 x 5 periodic box from the sharp 1.0 / 0.03 strip."""
+    L = lb.Lattice(64, FILM_NY, G_AB=G_AB, G1=G1, G2=G2, precision=precision)
+    L.set_fields(W.strip(64, FILM_NY, 32, noise=0.0))
+    L.step(steps)
+    rA = L.fields()["rho"][0][FILM_NY // 2]
+    return float(rA.max()), float(rA.min())
+
+
+def film_scan(G1: float, G2: float, G_AB: float, hs, nx: int = 128, steps: int = 8000, tau=(1.0, 1.0),
+              forcing: int = lb.LB_FORCING_GUO, precision: int = lb.LB_FP64) -> dict:
+    """Flat films of species B of widths hs between A regions in nx x 5
+    periodic boxes, all in one batch, started from sharp steps at the
+    coexisting densities of a flat interface, plus the same box at
+    h = nx / 2 (two independent interfaces: its gamma_f is 2 gamma).  After
+    `steps` steps: gamma_f(h) (Eq. 16, the sum of P_xx - P_yy over the box per
+    unit length), s(h) = gamma_f(h) - 2 gamma and Pi(h) (Eq. 18)."""
+    hs = [int(h) for h in hs]
+    hi, lo = coexistence(G1, G2, G_AB)
+    widths = hs + [nx // 2]
+    specs = [dict(nx=nx, ny=FILM_NY, tau=tau, G_AB=G_AB, G1=G1, G2=G2, forcing=forcing) for _ in widths]
+    b = lb.Batch(specs, precision=precision)
+    try:
+        b.set_config(lb.LB_MODE_FUSED, 4)
+        for i, h in enumerate(widths):
+            b.set_fields(i, np.ascontiguousarray(W.strip(nx, FILM_NY, h, noise=0.0, hi=hi, lo=lo)[::-1]))
+        b.step(steps)
+        gf = [tension_of(b.pressure_tensor(i)[0], FILM_NY, interfaces=1) for i in range(len(widths))]
+    finally:
+        b.close()
+    two_gamma = gf[-1]
+    s = np.array(gf[:-1]) - two_gamma
+    return {"h": np.array(hs, dtype=np.float64), "gamma_f": np.array(gf[:-1]), "two_gamma": two_gamma,
+            "s": s, "Pi": disjoining_pressure(np.array(hs, dtype=np.float64), s), "coexistence": (hi, lo)}
+
+
+def disjoining_pressure(h: np.ndarray, s: np.ndarray) -> np.ndarray:
+    """Pi(h_i) = s_i / h_i - int_{h_i}^inf s(h) / h^2 dh (Eq. 18, with
+    Pi(inf) = 0): the integral over the sampled widths by the trapezoid rule,
+    nothing beyond the widest film."""
+    h = np.asarray(h, dtype=np.float64)
+    s = np.asarray(s, dtype=np.float64)
+    f = s / h ** 2
+    seg = 0.5 * (f[1:] + f[:-1]) * np.diff(h)           # integral over [h_i, h_i+1]
+    tail = np.concatenate([np.cumsum(seg[::-1])[::-1], [0.0]])
+    return s / h - tail
+
+
+def flat_tension(G1: float, G2: float, G_AB: float, taus, forcing: int = lb.LB_FORCING_GUO, nx: int = 64,
+                 steps: int = 10000, precision: int = lb.LB_FP64) -> list[float]:
+    """gamma (Eq. 15) of a flat interface per (tau_A, tau_B) of taus: all in
+    one batch, started from the equilibrium of the strip at tau = 1 with Guo
+    forcing (so every run starts at rest)."""
+    L = lb.Lattice(nx, FILM_NY, G_AB=G_AB, G1=G1, G2=G2, precision=precision)
+    L.set_fields(W.strip(nx, FILM_NY, nx // 2, noise=0.0))
+    L.step(8000)
+    rho0 = L.fields()["rho"]
+    L.close()
+    specs = [dict(nx=nx, ny=FILM_NY, tau=t, G_AB=G_AB, G1=G1, G2=G2, forcing=forcing) for t in taus]
+    b = lb.Batch(specs, precision=precision)
+    try:
+        b.set_config(lb.LB_MODE_FUSED, 4)
+        for i in range(len(specs)):
+            b.set_fields(i, rho0)
+        b.step(steps)
+        return [tension_of(b.pressure_tensor(i)[0], FILM_NY) for i in range(len(specs))]
+    finally:
+        b.close()

@@ -37,6 +37,8 @@ def test_struct_layouts_match_header(lbmod):
     (dict(nx=16, ny=16, G1=float("inf")), "non-finite"),
     (dict(nx=16, ny=16, walls=2), "walls"),
     (dict(nx=16, ny=16, precision=7), "precision"),
+    (dict(nx=16, ny=16, forcing=2), "forcing"),
+    (dict(nx=16, ny=16, forcing=1, precision=1), "LB_FP64"),     # the velocity shift is FP64 only
 ])
 def test_invalid_parameters_rejected(lbmod, kw, needle):
     p = lbmod.make_params(**kw)

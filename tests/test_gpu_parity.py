@@ -17,9 +17,10 @@ err by ~1e-8 per step, a random forcing whose effect accumulates over the
 viscous relaxation time of the drop (R^2/nu ~ 900 steps): sqrt(900) * 1e-8 ~
 3e-7, i.e. 3e-5 of the 0.0095 spurious-current maximum at worst.  With the
 node's density split exactly into reference and offsets (no mass drift) the
-C1 droplet lands just under 1e-5.  Where droplets advect (the channel) an
-interface displaced by a velocity error moves densities too, and both fields
-are held to 1e-4."""
+C1 droplet lands just under 1e-5.  Where a body force drives the flow (the
+channel) the FP32 velocity also carries a systematic rounding bias growing
+with g t (see that test), and the fields are held to 5e-5 (u) and 2e-5
+(rho) there."""
 import numpy as np
 import pytest
 
@@ -129,7 +130,14 @@ def test_fp32_offset_c1_droplet(oracle_mod, lbmod):
 
 
 def test_fp32_offset_channel_mu_r(oracle_mod, lbmod):
-    """Body-forced channel with non-wetting walls: mu_r of FP32 within 1e-3."""
+    """Body-forced channel with non-wetting walls (g = 1e-5, ten times the
+    emulsion workloads' forcing): mu_r of FP32 within 1e-3 of the oracle
+    (measured 3.5e-6).  The FP32 velocity carries the systematic rounding bias
+    of the momentum-carrying terms under a body force, which grows with g t:
+    measured 4.1e-5 on u and 1.1e-5 on rho (the drops advect with the biased
+    flow), while an FP64 run with its initial densities perturbed by 1e-7
+    moves by only 2.9e-7 and 1.3e-7, so the excess is FP32 arithmetic, not
+    amplification; held to 5e-5 (u) and 2e-5 (rho)."""
     nx, ny = 96, 48
     rho, _, _, _ = W.hex_emulsion(nx, ny, 0.4, R=7.0, spread=1.0, gap=3.0, walls=True, seed=21)
     kw = dict(tau=(2.0, 1.0), g=(1e-5, 0.0), walls=1, wall_mode=1, wall_rho=(0.03, 1.0), **C6)
@@ -137,10 +145,8 @@ def test_fp32_offset_channel_mu_r(oracle_mod, lbmod):
     oo, og = o.observables(), g.observables()
     assert abs(og["mu_r"] - oo["mu_r"]) <= 1e-3 * abs(oo["mu_r"])
     fo, fg = o.fields(), g.fields()
-    # droplets advect here: a velocity error of ~3e-7 displaces an interface
-    # of slope ~0.3/node by ~3e-4 nodes over 1500 steps, i.e. ~1e-4 in rho
-    assert nrel(fg["rho"], fo["rho"]) <= 1e-4
-    assert nrel(fg["ubar"], fo["ubar"]) <= 1e-4
+    assert nrel(fg["rho"], fo["rho"]) <= 2e-5
+    assert nrel(fg["ubar"], fo["ubar"]) <= 5e-5
 
 
 def test_batch_matches_oracle_per_lattice(oracle_mod, lbmod):
