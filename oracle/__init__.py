@@ -59,6 +59,15 @@ class OrcParams(ctypes.Structure):
     ]
 
 
+class Orc3Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("pad", ctypes.c_int32),
+        ("tau", ctypes.c_double * 2),
+        ("G_AB", ctypes.c_double), ("G1", ctypes.c_double), ("G2", ctypes.c_double),
+        ("g", ctypes.c_double * 3),
+    ]
+
+
 def _load():
     global _lib
     with _lock:
@@ -87,6 +96,15 @@ def _load():
                                        P(ctypes.c_int32), P(ctypes.c_int32)]
             lib.orc_shift_forcing.argtypes = [d, d, d, d, d, d, dp]
             lib.orc_pressure_tensor.argtypes = [ctypes.c_void_p, dp]
+            lib.orc3_create.restype = ctypes.c_void_p
+            lib.orc3_create.argtypes = [P(Orc3Params)]
+            lib.orc3_destroy.argtypes = [ctypes.c_void_p]
+            lib.orc3_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
+            lib.orc3_set_fields.argtypes = [ctypes.c_void_p, dp, dp]
+            lib.orc3_get_f.argtypes = [ctypes.c_void_p, dp]
+            lib.orc3_fields.argtypes = [ctypes.c_void_p, dp, dp, dp]
+            lib.orc3_observables.argtypes = [ctypes.c_void_p, d, d, d, d, dp]
+            lib.orc3_tables.argtypes = [dp, P(ctypes.c_int32), dp]
             lib.orc_set_threads.restype = ctypes.c_int
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_bulk_pressure.restype = d
@@ -246,3 +264,76 @@ def disjoining_pressure(h, s) -> np.ndarray:
             tail += 0.5 * (g[j] + g[j + 1]) * (h[j + 1] - h[j])
         out[i] = s[i] / h[i] - tail
     return out
+
+
+OBS3_KEYS = ("massA", "massB", "momAx", "momAy", "momAz", "momBx", "momBy", "momBz", "dp", "R_eff", "umax",
+             "finite")
+
+
+class OracleSim3:
+    """The 3-D extension (D3Q19, 5^3 mid-range stencil), periodic in x, y, z.
+    Fields are [..][nz][ny][nx], populations [2][19][nz][ny][nx]."""
+
+    def __init__(self, nx, ny, nz, tau=(1.0, 1.0), G_AB=3.0, G1=-7.4, G2=6.4, g=(0.0, 0.0, 0.0)):
+        self.lib = _load()
+        p = Orc3Params()
+        p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+        p.tau[0], p.tau[1] = float(tau[0]), float(tau[1])
+        p.G_AB, p.G1, p.G2 = float(G_AB), float(G1), float(G2)
+        for a in range(3):
+            p.g[a] = float(g[a])
+        self.params = p
+        self.shape = (int(nz), int(ny), int(nx))
+        self.h = self.lib.orc3_create(ctypes.byref(p))
+        if not self.h:
+            raise ValueError("oracle rejected the parameters")
+
+    def close(self):
+        if self.h:
+            self.lib.orc3_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_fields(self, rho, u=None):
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        assert rho.shape == (2,) + self.shape
+        up = None
+        if u is not None:
+            u = np.ascontiguousarray(u, dtype=np.float64)
+            assert u.shape == (3,) + self.shape
+            up = _dptr(u)
+        self.lib.orc3_set_fields(self.h, _dptr(rho), up)
+
+    def step(self, n=1):
+        self.lib.orc3_step(self.h, int(n))
+
+    def get_f(self):
+        f = np.empty((2, 19) + self.shape)
+        self.lib.orc3_get_f(self.h, _dptr(f))
+        return f
+
+    def fields(self):
+        rho = np.empty((2,) + self.shape)
+        force = np.empty((2, 3) + self.shape)
+        ubar = np.empty((3,) + self.shape)
+        self.lib.orc3_fields(self.h, _dptr(rho), _dptr(force), _dptr(ubar))
+        return {"rho": rho, "force": force, "ubar": ubar}
+
+    def observables(self, probe=(0.0, 0.0, 0.0, 0.0)):
+        out = np.empty(12)
+        cx, cy, cz, R = probe
+        self.lib.orc3_observables(self.h, float(cx), float(cy), float(cz), float(R), _dptr(out))
+        return dict(zip(OBS3_KEYS, out.tolist()))
+
+
+def tables3() -> dict:
+    w = np.empty(19)
+    e = np.empty(57, np.int32)
+    q = np.empty(13)
+    _load().orc3_tables(_dptr(w), e.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dptr(q))
+    return {"w": w, "e": e.reshape(19, 3), "q": q}

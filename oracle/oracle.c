@@ -593,3 +593,322 @@ void orc_pressure_tensor(orc_sim *s, double *out)
             }
         }
 }
+
+/* ===========================================================================
+ * Three-dimensional extension (not in the paper, which is 2-D; Sec. II A).
+ * The same method on D3Q19 for the fluid, with the short-range sums of
+ * Eqs. (8), (9) over the D3Q19 neighbours (weights w: 1/3, 1/18, 1/36) and
+ * the mid-range sum of Eq. (8) over the 5 x 5 x 5 neighbourhood with weights
+ * q(|e|^2) isotropic to eighth order, normalised like the 2-D D2Q25 weights
+ * (sum q = 1, sum q e_x^2 = 1/3) and sharing their fourth moment
+ * (sum q e_x^4 = 4/7), the outermost shells |e|^2 = 9, 12 unweighted.
+ * Projected onto one axis both stencils are the 2-D ones, so a profile that
+ * varies along x only evolves exactly as in 2-D.  Periodic in x, y, z.
+ * ======================================================================== */
+
+static const int EX3[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+static const int EY3[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+static const int EZ3[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+
+/* w(|e|^2) of D3Q19 */
+static double w3_of(int e2)
+{
+    if (e2 == 0) return 1.0 / 3.0;
+    if (e2 == 1) return 1.0 / 18.0;
+    return 1.0 / 36.0;
+}
+
+/* q(|e|^2) of the 5 x 5 x 5 mid-range stencil */
+static double q3_of(int e2)
+{
+    switch (e2) {
+    case 0: return 47.0 / 90.0;
+    case 1: return 4.0 / 135.0;
+    case 2: return 1.0 / 63.0;
+    case 3: return 2.0 / 315.0;
+    case 4: return 5.0 / 1512.0;
+    case 5: return 1.0 / 945.0;
+    case 6: return 1.0 / 1890.0;
+    case 8: return 1.0 / 15120.0;
+    default: return 0.0;
+    }
+}
+
+typedef struct orc3_params {
+    int32_t nx, ny, nz, pad;
+    double tau[2];
+    double G_AB, G1, G2;
+    double g[3];
+} orc3_params;
+
+typedef struct orc3_sim {
+    orc3_params p;
+    long t;
+    double *f, *fn;     /* [2][19][nz][ny][nx] */
+    double *rho, *psi;  /* [2][nz][ny][nx] */
+    double *force;      /* [2][3][nz][ny][nx] */
+} orc3_sim;
+
+#define N3(s) ((size_t)(s)->p.nx * (s)->p.ny * (s)->p.nz)
+#define C3(s, x, y, z) ((((size_t)(z)) * (s)->p.ny + (y)) * (s)->p.nx + (x))
+
+void orc3_destroy(orc3_sim *s)
+{
+    if (!s) return;
+    free(s->f); free(s->fn); free(s->rho); free(s->psi); free(s->force);
+    free(s);
+}
+
+orc3_sim *orc3_create(const orc3_params *p)
+{
+    if (p->nx < 5 || p->ny < 5 || p->nz < 5 || !(p->tau[0] > 0.5) || !(p->tau[1] > 0.5)) return NULL;
+    orc3_sim *s = (orc3_sim *)calloc(1, sizeof(orc3_sim));
+    if (!s) return NULL;
+    s->p = *p;
+    size_t n = N3(s);
+    s->f = (double *)calloc(38 * n, sizeof(double));
+    s->fn = (double *)calloc(38 * n, sizeof(double));
+    s->rho = (double *)calloc(2 * n, sizeof(double));
+    s->psi = (double *)calloc(2 * n, sizeof(double));
+    s->force = (double *)calloc(6 * n, sizeof(double));
+    if (!s->f || !s->fn || !s->rho || !s->psi || !s->force) {
+        orc3_destroy(s);
+        return NULL;
+    }
+    return s;
+}
+
+/* Copies of the 3-D tables, for the table tests. */
+void orc3_tables(double w[19], int32_t e[57], double q[13])
+{
+    for (int i = 0; i < 19; ++i) {
+        w[i] = w3_of(EX3[i] * EX3[i] + EY3[i] * EY3[i] + EZ3[i] * EZ3[i]);
+        e[3 * i] = EX3[i];
+        e[3 * i + 1] = EY3[i];
+        e[3 * i + 2] = EZ3[i];
+    }
+    for (int k = 0; k < 13; ++k) q[k] = q3_of(k);
+}
+
+/* Eq. (2) in 3-D, cs^2 = 1/3 */
+static void eq3(double rho, const double u[3], double feq[19])
+{
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < 19; ++i) {
+        double eu = EX3[i] * u[0] + EY3[i] * u[1] + EZ3[i] * u[2];
+        feq[i] = w3_of(EX3[i] * EX3[i] + EY3[i] * EY3[i] + EZ3[i] * EZ3[i]) * rho
+               * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+    }
+}
+
+/* Eq. (5) in 3-D */
+static void guo3(double tau, const double u[3], const double F[3], double C[19])
+{
+    double omega = 1.0 / tau;
+    for (int i = 0; i < 19; ++i) {
+        double e[3] = {EX3[i], EY3[i], EZ3[i]};
+        double eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
+        double s = 0.0;
+        for (int a = 0; a < 3; ++a) s += (3.0 * (e[a] - u[a]) + 9.0 * eu * e[a]) * F[a];
+        C[i] = (1.0 - 0.5 * omega) * w3_of(EX3[i] * EX3[i] + EY3[i] * EY3[i] + EZ3[i] * EZ3[i]) * s;
+    }
+}
+
+static int wrap3(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+
+/* densities (Eq. 6), psi (Sec. II B) and the total force on each species
+ * (Eqs. 8, 9 and rho_k g) at every node */
+static void forces3(orc3_sim *s)
+{
+    int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
+    size_t n = N3(s);
+    for (int k = 0; k < 2; ++k)
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    size_t c = C3(s, x, y, z);
+                    double r = 0.0;
+                    for (int i = 0; i < 19; ++i) r += s->f[(k * 19 + i) * n + c];
+                    s->rho[k * n + c] = r;
+                    s->psi[k * n + c] = orc_psi(r);
+                }
+    const double G1 = s->p.G1, G2 = s->p.G2, GAB = s->p.G_AB;
+    for (int k = 0; k < 2; ++k)
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    size_t c = C3(s, x, y, z);
+                    int kb = 1 - k;
+                    double s1[3] = {0, 0, 0}, s2[3] = {0, 0, 0}, s3[3] = {0, 0, 0};
+                    for (int i = 0; i < 19; ++i) {
+                        size_t d = C3(s, wrap3(x + EX3[i], nx), wrap3(y + EY3[i], ny), wrap3(z + EZ3[i], nz));
+                        double w = w3_of(EX3[i] * EX3[i] + EY3[i] * EY3[i] + EZ3[i] * EZ3[i]);
+                        double a = w * s->psi[k * n + d], b = w * s->rho[kb * n + d];
+                        s1[0] += a * EX3[i]; s1[1] += a * EY3[i]; s1[2] += a * EZ3[i];
+                        s3[0] += b * EX3[i]; s3[1] += b * EY3[i]; s3[2] += b * EZ3[i];
+                    }
+                    for (int dz = -2; dz <= 2; ++dz)
+                        for (int dy = -2; dy <= 2; ++dy)
+                            for (int dx = -2; dx <= 2; ++dx) {
+                                size_t d = C3(s, wrap3(x + dx, nx), wrap3(y + dy, ny), wrap3(z + dz, nz));
+                                double a = q3_of(dx * dx + dy * dy + dz * dz) * s->psi[k * n + d];
+                                s2[0] += a * dx; s2[1] += a * dy; s2[2] += a * dz;
+                            }
+                    double psi = s->psi[k * n + c], rho = s->rho[k * n + c];
+                    for (int a = 0; a < 3; ++a)
+                        s->force[(k * 3 + a) * n + c] = -G1 * psi * s1[a] - G2 * psi * s2[a] - GAB * rho * s3[a]
+                                                      + rho * s->p.g[a];
+                }
+}
+
+/* Eq. (6) momenta with half force and the common velocity of Eq. (3) */
+static void moments3(const orc3_sim *s, size_t c, double rho[2], double m[2][3], double ueq[3])
+{
+    size_t n = N3(s);
+    for (int k = 0; k < 2; ++k) {
+        double j[3] = {0, 0, 0};
+        for (int i = 0; i < 19; ++i) {
+            double fi = s->f[(k * 19 + i) * n + c];
+            j[0] += fi * EX3[i]; j[1] += fi * EY3[i]; j[2] += fi * EZ3[i];
+        }
+        rho[k] = s->rho[k * n + c];
+        for (int a = 0; a < 3; ++a) m[k][a] = j[a] + 0.5 * s->force[(k * 3 + a) * n + c];
+    }
+    double om0 = 1.0 / s->p.tau[0], om1 = 1.0 / s->p.tau[1];
+    double den = om0 * rho[0] + om1 * rho[1];
+    for (int a = 0; a < 3; ++a) ueq[a] = (om0 * m[0][a] + om1 * m[1][a]) / den;
+}
+
+static void step3_once(orc3_sim *s)
+{
+    int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
+    size_t n = N3(s);
+    forces3(s);
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t c = C3(s, x, y, z);
+                double rho[2], m[2][3], ueq[3];
+                moments3(s, c, rho, m, ueq);
+                for (int k = 0; k < 2; ++k) {
+                    double omega = 1.0 / s->p.tau[k], feq[19], C[19];
+                    double F[3] = {s->force[(k * 3) * n + c], s->force[(k * 3 + 1) * n + c], s->force[(k * 3 + 2) * n + c]};
+                    eq3(rho[k], ueq, feq);
+                    guo3(s->p.tau[k], ueq, F, C);
+                    for (int i = 0; i < 19; ++i) {
+                        double fi = s->f[(k * 19 + i) * n + c];
+                        size_t d = C3(s, wrap3(x + EX3[i], nx), wrap3(y + EY3[i], ny), wrap3(z + EZ3[i], nz));
+                        s->fn[(k * 19 + i) * n + d] = fi - omega * (fi - feq[i]) + C[i];
+                    }
+                }
+            }
+    double *tmp = s->f;
+    s->f = s->fn;
+    s->fn = tmp;
+    s->t += 1;
+}
+
+void orc3_step(orc3_sim *s, long n)
+{
+    for (long t = 0; t < n; ++t) step3_once(s);
+}
+
+/* f = f^eq(rho_k, u) from rho [2][nz][ny][nx] and an optional u [3][nz][ny][nx] */
+void orc3_set_fields(orc3_sim *s, const double *rho, const double *u)
+{
+    size_t n = N3(s);
+    for (size_t c = 0; c < n; ++c)
+        for (int k = 0; k < 2; ++k) {
+            double uu[3] = {u ? u[c] : 0.0, u ? u[n + c] : 0.0, u ? u[2 * n + c] : 0.0};
+            double feq[19];
+            eq3(rho[k * n + c], uu, feq);
+            for (int i = 0; i < 19; ++i) s->f[(k * 19 + i) * n + c] = feq[i];
+        }
+    s->t = 0;
+}
+
+void orc3_get_f(const orc3_sim *s, double *f) { memcpy(f, s->f, sizeof(double) * 38 * N3(s)); }
+
+/* rho [2][nz][ny][nx], force [2][3][..], ubar [3][..] (Eq. 7); NULL skips */
+void orc3_fields(orc3_sim *s, double *rho, double *force, double *ubar)
+{
+    size_t n = N3(s);
+    forces3(s);
+    for (size_t c = 0; c < n; ++c) {
+        double r[2], m[2][3], ue[3];
+        moments3(s, c, r, m, ue);
+        if (rho) { rho[c] = r[0]; rho[n + c] = r[1]; }
+        if (force)
+            for (int q = 0; q < 6; ++q) force[q * n + c] = s->force[q * n + c];
+        if (ubar)
+            for (int a = 0; a < 3; ++a) ubar[a * n + c] = (m[0][a] + m[1][a]) / (r[0] + r[1]);
+    }
+}
+
+/* Observables: out[0..1] mass of A, B; out[2..7] momentum of A (x, y, z), B
+ * (x, y, z) with half force; out[8] dp = <p_b>_in - <p_b>_out around the
+ * probe sphere (inside r < R/2, outside r > R + 6, minimum image); out[9]
+ * R_eff = (3 (M_A - rho_out N) / (4 pi (rho_in - rho_out)))^(1/3), the
+ * equimolar radius; out[10] max |ubar|; out[11] 1 if every density and
+ * velocity is finite.  R <= 0: out[8], out[9] NaN. */
+void orc3_observables(orc3_sim *s, double cx, double cy, double cz, double R, double out[12])
+{
+    int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
+    size_t n = N3(s);
+    double *rho = (double *)malloc(sizeof(double) * 2 * n), *ub = (double *)malloc(sizeof(double) * 3 * n);
+    orc3_fields(s, rho, NULL, ub);
+    double mass[2] = {0, 0}, mom[6] = {0, 0, 0, 0, 0, 0}, umax = 0.0;
+    double pin = 0, pout = 0, ain = 0, aout = 0, nin = 0, nout = 0;
+    int finite = 1;
+    orc_params pp;
+    memset(&pp, 0, sizeof pp);
+    pp.G1 = s->p.G1; pp.G2 = s->p.G2; pp.G_AB = s->p.G_AB;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t c = C3(s, x, y, z);
+                double r[2], m[2][3], ue[3];
+                moments3(s, c, r, m, ue);
+                for (int k = 0; k < 2; ++k) {
+                    mass[k] += rho[k * n + c];
+                    for (int a = 0; a < 3; ++a) mom[3 * k + a] += m[k][a];
+                }
+                double u2 = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    if (!isfinite(ub[a * n + c])) finite = 0;
+                    u2 += ub[a * n + c] * ub[a * n + c];
+                }
+                if (!isfinite(rho[c]) || !isfinite(rho[n + c])) finite = 0;
+                if (sqrt(u2) > umax) umax = sqrt(u2);
+                if (R > 0.0) {
+                    double d[3] = {fabs(x - cx), fabs(y - cy), fabs(z - cz)};
+                    int L[3] = {nx, ny, nz};
+                    double r2 = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        if (d[a] > 0.5 * L[a]) d[a] = L[a] - d[a];
+                        r2 += d[a] * d[a];
+                    }
+                    double rr = sqrt(r2), pb = orc_bulk_pressure(&pp, rho[c], rho[n + c]);
+                    if (rr < 0.5 * R) { pin += pb; ain += rho[c]; nin += 1.0; }
+                    if (rr > R + 6.0) { pout += pb; aout += rho[c]; nout += 1.0; }
+                }
+            }
+    out[0] = mass[0];
+    out[1] = mass[1];
+    for (int a = 0; a < 6; ++a) out[2 + a] = mom[a];
+    if (R > 0.0 && nin > 0.0 && nout > 0.0) {
+        double rin = ain / nin, rout = aout / nout;
+        out[8] = pin / nin - pout / nout;
+        out[9] = cbrt(3.0 * (mass[0] - rout * (double)n) / (4.0 * ORC_PI * (rin - rout)));
+    } else {
+        out[8] = NAN;
+        out[9] = NAN;
+    }
+    out[10] = umax;
+    out[11] = finite ? 1.0 : 0.0;
+    free(rho);
+    free(ub);
+}

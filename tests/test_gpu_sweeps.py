@@ -97,3 +97,32 @@ def test_relative_viscosity_rises_with_droplet_viscosity(sweeps):
     g = sweeps.body_force(37.0, 220)
     q0 = g * (220 ** 3 + 110) / (12.0 / 6.0)
     assert abs(ref["Q"] / q0 - 1.0) <= 0.01, (ref["Q"], q0)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
+def test_sweep_lattices_match_the_oracle(oracle_mod, precision, tol):
+    """One lattice of each sweep against the oracle over 300 steps, in the
+    sweeps' own configuration (FP32: TMA-staged step, tile height 8): a
+    Table I Laplace drop (G1 = 10, G2 = -11, G_AB = 5.0, R = 24 on 192^2) and a
+    rheology channel (5 x 5 drops at area fraction 0.45 in 220 x 220,
+    non-wetting walls, reduced forcing 37, M = 1/3), rho and u normwise."""
+    from paper_1806_06943_gb300 import lb, sweeps as S
+    from paper_1806_06943_gb300 import workloads as W
+    n = S.laplace_side(24.0)
+    drop = (n, n, W.droplet(n, n, 24.0, seed=W.BASE_SEED + 11),
+            dict(G_AB=5.0, G1=10.0, G2=-11.0))
+    rho_c, _ = S.droplet_array(220, 5, float(np.sqrt(0.45 * 220 * 220 / (25 * np.pi))), seed=W.BASE_SEED + 5)
+    chan = (220, 220, rho_c, dict(G_AB=3.0, G1=-7.4, G2=6.4, tau=(S.tau_for_ratio(1.0 / 3.0), 1.0),
+                                  g=(S.body_force(37.0, 220), 0.0), walls=1, wall_mode=1, wall_rho=(0.03, 1.0)))
+    for nx, ny, rho, kw in (drop, chan):
+        o = oracle_mod.OracleSim(nx, ny, **kw)
+        o.set_fields(rho)
+        o.step(300)
+        g = lb.Lattice(nx, ny, precision=precision, **kw)
+        g.set_config(lb.LB_MODE_TMA if precision == lb.LB_FP32 else lb.LB_MODE_FUSED, 8)
+        g.set_fields(rho)
+        g.step(300)
+        fo, fg = o.fields(), g.fields()
+        for k in ("rho", "ubar"):
+            err = np.max(np.abs(fg[k] - fo[k])) / np.max(np.abs(fo[k]))
+            assert err <= tol, (nx, ny, k, err)
