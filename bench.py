@@ -40,6 +40,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -519,6 +521,36 @@ def main():
                          "collide_frac_design": BYTES_COLLIDE[prec] * n4 / (m2[1] * 1e-3) / 1e9 / peak}
             del L
         out["large_dense_4096"] = big
+
+        # the 3-D extension: a periodic 160^3 emulsion of spheres (radius 8,
+        # viscosity ratio 5), FP32 offsets and FP64, two launches per step
+        three = {}
+        n3 = 160
+        z3, y3, x3 = [a.astype(np.float64) for a in np.meshgrid(np.arange(n3), np.arange(n3), np.arange(n3),
+                                                                   indexing="ij")]
+        m3 = np.zeros((n3, n3, n3), dtype=bool)
+        for cz in range(10, n3, 20):
+            for cy in range(10, n3, 20):
+                for cx in range(10, n3, 20):
+                    m3 |= (x3 - cx) ** 2 + (y3 - cy) ** 2 + (z3 - cz) ** 2 < 64.0
+        rho3 = np.empty((2, n3, n3, n3))
+        rho3[0] = np.where(m3, 1.0, 0.03)
+        rho3[1] = np.where(m3, 0.03, 1.0)
+        del x3, y3, z3
+        for prec, name in ((lb.LB_FP32, "fp32"), (lb.LB_FP64, "fp64")):
+            L3 = lb.Lattice3(n3, n3, n3, tau=(3.0, 1.0), precision=prec, stream=sptr, **C6)
+            L3.set_fields(rho3)
+            L3.profile(3, flush.data_ptr(), FLUSH_BYTES)
+            m = L3.profile(10 if prec == lb.LB_FP32 else 4, flush.data_ptr(), FLUSH_BYTES)
+            nodes = n3 ** 3
+            floor3 = 2 * 38 * (4 if prec == lb.LB_FP32 else 8)
+            three[name] = {"mlups": nodes / (m[2] * 1e-3) / 1e6, "ms_per_step": m[2], "density_ms": m[0],
+                           "collide_ms": m[1], "algorithmic_bytes_per_site": floor3,
+                           "step_frac_floor": floor3 * nodes / (m[2] * 1e-3) / 1e9 / peak,
+                           "phi_achieved": float(m3.mean())}
+            del L3
+        out["three_d_160"] = three
+        del rho3, m3
 
         # end to end through the public API with host buffers: per e2e step,
         # upload every lattice's initial fields from pinned host memory, run

@@ -335,6 +335,68 @@ int lb_batch_autotune(lb_batch *b, int32_t trial_steps, const char *cache_path, 
  * LB_ETIMEOUT; -1 turns the hook off. */
 int lb_batch_set_wait_limit(lb_batch *b, double seconds, int32_t drop_tile);
 
+/* ---- three-dimensional extension ------------------------------------------- */
+
+/* The method in 3-D (the paper is 2-D): D3Q19 fluid (weights 1/3, 1/18,
+ * 1/36) with the BGK + Guo step of Eqs. (1)-(3), (5), (6); the short-range
+ * sums of Eqs. (8), (9) over the D3Q19 neighbours; the mid-range sum of
+ * Eq. (8) over the 5 x 5 x 5 neighbourhood with weights q(|e|^2) = 47/90,
+ * 4/135, 1/63, 2/315, 5/1512, 1/945, 1/1890, 1/15120 for |e|^2 = 0..6, 8 (0
+ * for 9, 12): isotropic to eighth order, with the D2Q25 weights' second and
+ * fourth moments, so that a profile varying along one axis evolves exactly
+ * as in 2-D.  Periodic in x, y and z; no walls.  Host arrays are
+ * [..][nz][ny][nx], x fastest; a species field is [2][nz][ny][nx], a vector
+ * field [3][nz][ny][nx], populations [2][19][nz][ny][nx] with the direction
+ * order rest, (+-1,0,0), (0,+-1,0), (0,0,+-1), (1,1,0), (-1,-1,0), (1,-1,0),
+ * (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1),
+ * (0,1,-1), (0,-1,1).  One time step is two launches (density pass, fused
+ * force / collision / push); LB_FP32 stores offsets from the node's previous
+ * density as the 2-D form does.  Same error conventions as above. */
+typedef struct lb3_params {
+    int32_t nx, ny, nz;   /* each >= 5 */
+    int32_t precision;    /* LB_FP64 or LB_FP32 */
+    double tau[2];        /* > 1/2 */
+    double G_AB, G1, G2;  /* Eqs. (8), (9) */
+    double g[3];          /* body acceleration; the force on species k is rho_k g */
+    void *stream;         /* cudaStream_t, or NULL for a stream of its own */
+} lb3_params;
+
+/* mass[k], mom[k][a] (half force, Eq. 6), dp_laplace and R_eff (equimolar
+ * sphere radius, (3 V / 4 pi)^(1/3)) around the probe (inside r < R/2,
+ * outside r > R + 6; NaN without probe), umax = max |ubar| (Eq. 7), finite. */
+typedef struct lb3_obs {
+    int64_t t;
+    double mass[2];
+    double mom[2][3];
+    double dp_laplace;
+    double R_eff;
+    double umax;
+    int32_t finite;
+    int32_t reserved;
+} lb3_obs;
+
+typedef struct lb3_handle lb3_handle;
+
+int lb3_create(const lb3_params *p, lb3_handle **out);
+void lb3_destroy(lb3_handle *h);
+/* f = f^eq(rho_k, u) (Eq. 2) and t = 0; rho host [2][nz][ny][nx], u host
+ * [3][nz][ny][nx] or NULL.  Synchronous. */
+int lb3_set_fields(lb3_handle *h, const double *rho, const double *u);
+/* Advance n >= 0 steps (asynchronous, as lb_step). */
+int lb3_step(lb3_handle *h, int64_t n);
+int64_t lb3_time(const lb3_handle *h);
+/* Sphere probe for the Laplace observables (R <= 0 removes it). */
+int lb3_set_probe(lb3_handle *h, double cx, double cy, double cz, double R);
+/* Observables at the current time, sums in FP64.  Synchronises; LB_EUNSTABLE
+ * (with *o filled) if a value is not finite. */
+int lb3_observables(lb3_handle *h, lb3_obs *o);
+/* rho host [2][nz][ny][nx] and ubar host [3][nz][ny][nx]; NULL skips one. */
+int lb3_get_fields(lb3_handle *h, double *rho, double *ubar);
+/* Populations as FP64 host [2][19][nz][ny][nx] (LB_FP32: w_i R added back). */
+int lb3_get_populations(lb3_handle *h, double *f);
+/* As lb_profile: ms[0] density pass, ms[1] fused kernel, ms[2] whole step. */
+int lb3_profile(lb3_handle *h, int32_t nsteps, void *flush_buf, size_t flush_bytes, double ms[3]);
+
 /* ---- device diagnostics ------------------------------------------------------ */
 
 /* Measured FP64 fused multiply-add throughput of the current device in

@@ -33,6 +33,9 @@ UNITS = {
     "lb_noalloc.cu": ["-fmad=false"],
     "lb_adjoint.cu": ["-fmad=false"],
     "lb_device.cu": [],
+    "lb3_api.cu": [],
+    "lb3_fp64.cu": ["-fmad=false"],
+    "lb3_fp32.cu": [],
 }
 
 

@@ -68,6 +68,34 @@ class lb_obs(ctypes.Structure):
         }
 
 
+class lb3_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("tau", ctypes.c_double * 2),
+        ("G_AB", ctypes.c_double), ("G1", ctypes.c_double), ("G2", ctypes.c_double),
+        ("g", ctypes.c_double * 3),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class lb3_obs(ctypes.Structure):
+    _fields_ = [
+        ("t", ctypes.c_int64),
+        ("mass", ctypes.c_double * 2),
+        ("mom", (ctypes.c_double * 3) * 2),
+        ("dp_laplace", ctypes.c_double), ("R_eff", ctypes.c_double), ("umax", ctypes.c_double),
+        ("finite", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+    def to_dict(self) -> dict:
+        d = {"t": self.t, "massA": self.mass[0], "massB": self.mass[1], "dp": self.dp_laplace, "R_eff": self.R_eff,
+             "umax": self.umax, "finite": float(self.finite)}
+        for k, sp in enumerate("AB"):
+            for a, ax in enumerate("xyz"):
+                d["mom" + sp + ax] = self.mom[k][a]
+        return d
+
+
 _P = ctypes.POINTER
 _d = ctypes.c_double
 _dp = _P(_d)
@@ -113,6 +141,16 @@ SIGNATURES = {
     "lb_observables_static": (ctypes.c_int, [_P(lb_params), _vp, _d, _d, _d, _vp]),
     "lb_device_fp64_peak": (ctypes.c_int, [_i32, _dp]),
     "lb_pressure_tensor": (ctypes.c_int, [_vp, _vp, _vp]),
+    "lb3_create": (ctypes.c_int, [_P(lb3_params), _P(_vp)]),
+    "lb3_destroy": (None, [_vp]),
+    "lb3_set_fields": (ctypes.c_int, [_vp, _vp, _vp]),
+    "lb3_step": (ctypes.c_int, [_vp, _i64]),
+    "lb3_time": (_i64, [_vp]),
+    "lb3_set_probe": (ctypes.c_int, [_vp, _d, _d, _d, _d]),
+    "lb3_observables": (ctypes.c_int, [_vp, _P(lb3_obs)]),
+    "lb3_get_fields": (ctypes.c_int, [_vp, _vp, _vp]),
+    "lb3_get_populations": (ctypes.c_int, [_vp, _vp]),
+    "lb3_profile": (ctypes.c_int, [_vp, _i32, _vp, _sz, _dp]),
     "lb_batch_pressure_tensor": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
 }
 
@@ -128,7 +166,7 @@ def header_functions() -> list[str]:
     """Names of the functions include/lb.h declares."""
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lb_[a-z0-9_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(lb3?_[a-z0-9_]+)\s*\(", src)))
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -391,3 +429,69 @@ class Batch:
         rho, mom, ubar = np.empty((2,) + n), np.empty((2, 2) + n), np.empty((2,) + n)
         _check(LIB.lb_batch_get_fields(self.b, int(i), rho.ctypes.data, mom.ctypes.data, ubar.ctypes.data))
         return {"rho": rho, "mom": mom, "ubar": ubar}
+
+
+class Lattice3:
+    """One 3-D lattice (D3Q19, 5^3 mid-range stencil, periodic) behind an
+    lb3_handle.  Fields are numpy float64 [..][nz][ny][nx]."""
+
+    def __init__(self, nx, ny, nz, tau=(1.0, 1.0), G_AB=3.0, G1=-7.4, G2=6.4, g=(0.0, 0.0, 0.0),
+                 precision=LB_FP64, stream=None):
+        p = lb3_params()
+        p.nx, p.ny, p.nz, p.precision = int(nx), int(ny), int(nz), int(precision)
+        p.tau[0], p.tau[1] = float(tau[0]), float(tau[1])
+        p.G_AB, p.G1, p.G2 = float(G_AB), float(G1), float(G2)
+        for a in range(3):
+            p.g[a] = float(g[a])
+        p.stream = stream
+        self.params = p
+        self.shape = (int(nz), int(ny), int(nx))
+        h = _vp()
+        _check(LIB.lb3_create(ctypes.byref(p), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            LIB.lb3_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def t(self) -> int:
+        return LIB.lb3_time(self.h)
+
+    def set_fields(self, rho, u=None):
+        _check(LIB.lb3_set_fields(self.h, _host_ptr(rho, (2,) + self.shape), _host_ptr(u, (3,) + self.shape)))
+
+    def step(self, n: int = 1):
+        _check(LIB.lb3_step(self.h, int(n)))
+
+    def set_probe(self, cx, cy, cz, R):
+        _check(LIB.lb3_set_probe(self.h, float(cx), float(cy), float(cz), float(R)))
+
+    def observables(self, check: bool = True) -> dict:
+        o = lb3_obs()
+        rc = LIB.lb3_observables(self.h, ctypes.byref(o))
+        if check or rc != LB_EUNSTABLE:
+            _check(rc)
+        return o.to_dict()
+
+    def fields(self) -> dict:
+        rho, ubar = np.empty((2,) + self.shape), np.empty((3,) + self.shape)
+        _check(LIB.lb3_get_fields(self.h, rho.ctypes.data, ubar.ctypes.data))
+        return {"rho": rho, "ubar": ubar}
+
+    def get_populations(self) -> np.ndarray:
+        f = np.empty((2, 19) + self.shape)
+        _check(LIB.lb3_get_populations(self.h, f.ctypes.data))
+        return f
+
+    def profile(self, nsteps: int, flush_ptr=None, flush_bytes: int = 0) -> tuple:
+        ms = (ctypes.c_double * 3)()
+        _check(LIB.lb3_profile(self.h, int(nsteps), flush_ptr, int(flush_bytes), ms))
+        return tuple(ms)

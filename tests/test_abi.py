@@ -65,3 +65,15 @@ def test_batch_rejects_mixed_precision(lbmod):
     b = ctypes.c_void_p()
     assert lbmod.LIB.lb_batch_create(arr, 2, ctypes.byref(b)) == lbmod.LB_EINVAL
     assert lbmod.LIB.lb_batch_create(arr, 0, ctypes.byref(b)) == lbmod.LB_EINVAL
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(nx=4, ny=8, nz=8), "nz must be >= 5"),
+    (dict(nx=8, ny=8, nz=8, tau=(0.5, 1.0)), "tau"),
+    (dict(nx=8, ny=8, nz=8, G1=float("nan")), "non-finite"),
+    (dict(nx=8, ny=8, nz=8, precision=3), "precision"),
+])
+def test_3d_parameters_rejected_before_any_cuda_call(lbmod, kw, needle):
+    with pytest.raises(lbmod.LBError) as ei:
+        lbmod.Lattice3(**kw)
+    assert ei.value.code == lbmod.LB_EINVAL and needle in str(ei.value)

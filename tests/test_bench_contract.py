@@ -35,11 +35,15 @@ def test_traffic_is_keyed_by_kernel_workload_and_sources():
     import bench
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
         entries = json.load(f)
+    sha = bench.kernel_source_sha1()
+    for e in entries:
+        got = bench.kernel_traffic(e["workload"], e["kernel"])
+        current = [d for d in entries if d["workload"] == e["workload"] and d["kernel"] == e["kernel"]
+                   and d["kernel_source_sha1"] == sha]
+        if current:
+            assert got == float(current[0]["bytes_per_launch"])
+        else:
+            assert got is None
     e = entries[0]
-    got = bench.kernel_traffic(e["workload"], e["kernel"])
-    if e["kernel_source_sha1"] == bench.kernel_source_sha1():
-        assert got == float(e["bytes_per_launch"])
-    else:
-        assert got is None
     assert bench.kernel_traffic("no_such_workload", e["kernel"]) is None
     assert bench.kernel_traffic(e["workload"], "k_collide<float, 4>") is None
