@@ -95,6 +95,12 @@ struct Stage3 {
     real rho[2][SZ][SY][SX];
     real psi[2][SZ][SY][SX];
 };
+static_assert(sizeof(Stage3<float>) % 16 == 0 && sizeof(Stage3<double>) % 16 == 0, "partials stay aligned");
+
+template <typename real>
+constexpr size_t kCollideSmem3 = sizeof(Stage3<real>);
+template <typename real>
+constexpr size_t kObserveSmem3 = sizeof(Stage3<real>) + (kThreads / 32) * kNumAcc * sizeof(double);
 
 // rho and psi of the tile (x0, y0, z0) and its 2-node halo from density copy
 // `rho` (periodic copies across every face).
@@ -142,8 +148,7 @@ __device__ __forceinline__ void q19_sum(const real (*s)[SY][SX], int cx, int cy,
 }
 
 // sum_j q_j s(x + e_j) e_j over the 5 x 5 x 5 neighbourhood (FP64: raster
-// order dz, dy, dx; FP32: differences of opposite neighbours over the half
-// space that comes first in raster order's reverse)
+// order dz, dy, dx; FP32: differences of opposite neighbours, each pair once)
 template <typename real>
 __device__ __forceinline__ void q125_sum(const real (*s)[SY][SX], int cx, int cy, int cz, real (&out)[3])
 {
@@ -203,10 +208,14 @@ __global__ void __launch_bounds__(kThreads) k3_density(const Lat3<real> L, int p
     }
 }
 
+// Dynamic shared memory of the staging kernels (the FP64 stage is above the
+// 48 KB of static shared memory): the stage, then the observation partials.
+extern __shared__ __align__(16) unsigned char lb3_smem[];
+
 template <typename real>
 __global__ void __launch_bounds__(kThreads) k3_collide(const Lat3<real> L, int parity)
 {
-    __shared__ Stage3<real> sm;
+    Stage3<real> &sm = *reinterpret_cast<Stage3<real> *>(lb3_smem);
     int x0, y0, z0;
     tile_origin(L.tiles_x, L.tiles_y, blockIdx.x, x0, y0, z0);
     const int tid = (threadIdx.z * TY + threadIdx.y) * TX + threadIdx.x;
@@ -305,8 +314,8 @@ template <typename real>
 __global__ void __launch_bounds__(kThreads) k3_observe(const Lat3<real> L, int parity, double *__restrict__ partials,
                                                        double *__restrict__ out_rho, double *__restrict__ out_u)
 {
-    __shared__ Stage3<real> sm;
-    __shared__ double sacc[kThreads / 32][kNumAcc];
+    Stage3<real> &sm = *reinterpret_cast<Stage3<real> *>(lb3_smem);
+    double(*sacc)[kNumAcc] = reinterpret_cast<double(*)[kNumAcc]>(lb3_smem + sizeof(Stage3<real>));
     int x0, y0, z0;
     tile_origin(L.tiles_x, L.tiles_y, blockIdx.x, x0, y0, z0);
     const int tid = (threadIdx.z * TY + threadIdx.y) * TX + threadIdx.x;

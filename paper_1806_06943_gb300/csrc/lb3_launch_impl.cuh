@@ -18,7 +18,10 @@ template <typename real>
 cudaError_t Launch3<real>::collide(const Lat3<real> &L, int parity, cudaStream_t s)
 {
     const unsigned n = (unsigned)L.tiles_x * L.tiles_y * L.tiles_z;
-    k3_collide<real><<<n, dim3(TX, TY, TZ), 0, s>>>(L, parity);
+    cudaError_t e = cudaFuncSetAttribute(k3_collide<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kCollideSmem3<real>);
+    if (e != cudaSuccess) return e;
+    k3_collide<real><<<n, dim3(TX, TY, TZ), kCollideSmem3<real>, s>>>(L, parity);
     return cudaGetLastError();
 }
 
@@ -35,7 +38,10 @@ cudaError_t Launch3<real>::observe(const Lat3<real> &L, int parity, double *part
                                    cudaStream_t s)
 {
     const unsigned n = (unsigned)L.tiles_x * L.tiles_y * L.tiles_z;
-    k3_observe<real><<<n, dim3(TX, TY, TZ), 0, s>>>(L, parity, partials, rho, u);
+    cudaError_t e = cudaFuncSetAttribute(k3_observe<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kObserveSmem3<real>);
+    if (e != cudaSuccess) return e;
+    k3_observe<real><<<n, dim3(TX, TY, TZ), kObserveSmem3<real>, s>>>(L, parity, partials, rho, u);
     return cudaGetLastError();
 }
 
