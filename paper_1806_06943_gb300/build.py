@@ -1,7 +1,9 @@
 """Build the CUDA library liblb.so in-tree for sm_103a (GB300).
 
 Each translation unit compiles in parallel with nvcc; the FP64 kernels are
-compiled without fused multiply-add so they round exactly as written.  The
+compiled without fused multiply-add contraction so they round exactly as
+written (the FP32 kernels spell every rounding out with intrinsics, which
+are never contracted).  The
 result is linked with the static CUDA runtime into
 paper_1806_06943_gb300/liblb.so.  Rebuilds only when a source is newer than
 the library.

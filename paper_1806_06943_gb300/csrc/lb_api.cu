@@ -99,12 +99,19 @@ void fill_lat(lbk::Lat<real> &L, const lb_params &p)
         L.omega[k] = (real)omega;
         L.tau[k] = (real)p.tau[k];
         for (int c = 0; c < 3; ++c) L.aw[k][c] = (real)((1.0 - 0.5 * omega) * wcls[c]);
+        for (int c = 0; c < 3; ++c) L.aw3[k][c] = (real)3 * L.aw[k][c];
         L.g[k] = (real)p.g[k];
         L.wall_rho[k] = (real)p.wall_rho[k];
     }
     L.G1 = (real)p.G1;
     L.G2 = (real)p.G2;
     L.GAB = (real)p.G_AB;
+    // the combined psi-sum weights of Eq. (8) on the inner ring,
+    // c(|e|^2) = G1 w(|e|^2) + G2 p(|e|^2) for |e|^2 = 1, 2, and G2 for the
+    // outer ring, negated
+    L.cw[0] = (real)(-(p.G1 / 9.0 + p.G2 * (4.0 / 63.0)));
+    L.cw[1] = (real)(-(p.G1 / 36.0 + p.G2 * (4.0 / 135.0)));
+    L.cw[2] = (real)(-p.G2);
     L.tau_B = p.tau[1];
     L.g_x = p.g[0];
 }

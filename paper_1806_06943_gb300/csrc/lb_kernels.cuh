@@ -29,6 +29,9 @@
 #include <math.h>
 
 #include "lb_types.h"
+#include "lb_vops.cuh"
+
+#include <type_traits>
 
 namespace lbk {
 
@@ -68,6 +71,11 @@ __host__ __device__ constexpr double p25(int e2)
     return e2 == 0 ? 247.0 / 420.0 : e2 == 1 ? 4.0 / 63.0 : e2 == 2 ? 4.0 / 135.0 : e2 == 4 ? 1.0 / 180.0
          : e2 == 5 ? 2.0 / 945.0 : e2 == 8 ? 1.0 / 15120.0 : 0.0;
 }
+// the same weights rounded to FP32
+struct P25f {
+    __host__ __device__ constexpr float operator()(int e2) const { return (float)p25(e2); }
+};
+constexpr P25f p25f{};
 
 template <typename real> __device__ __forceinline__ real psi_of(real r);
 // psi = rho0 (1 - exp(-rho/rho0)), rho0 = 1 (Sec. II B)
@@ -151,12 +159,9 @@ __device__ __forceinline__ void q9_sum(const real (*s)[SW], int cx, int cy, real
         sx = ((((a1 - a3) + a5) - a6) - a7) + a8;
         sy = ((((a2 - a4) + a5) + a6) - a7) - a8;
     } else {
-        const real dE = s[cy][cx + 1] - s[cy][cx - 1];
-        const real dN = s[cy + 1][cx] - s[cy - 1][cx];
-        const real d1 = s[cy + 1][cx + 1] - s[cy - 1][cx - 1];   // (1,1) - (-1,-1)
-        const real d2 = s[cy - 1][cx + 1] - s[cy + 1][cx - 1];   // (1,-1) - (-1,1)
-        sx = W1 * dE + W2 * (d1 + d2);
-        sy = W1 * dN + W2 * (d1 - d2);
+        (void)W1;
+        (void)W2;
+        vq9<float>([&](int dy, int dx) { return s[cy + dy][cx + dx]; }, sx, sy);
     }
 }
 
@@ -178,41 +183,33 @@ __device__ __forceinline__ void q25_sum(const real (*s)[SW], int cx, int cy, rea
             if (dy != 0) sy += pp * (real)dy;
         }
     } else {
-        real ax = (real)0, ay = (real)0;
-#pragma unroll
-        for (int a = 1; a <= 2; ++a) {   // axis classes (a,0) and (0,a)
-            const real p = (real)(p25(a * a) * a);
-            ax += p * (s[cy][cx + a] - s[cy][cx - a]);
-            ay += p * (s[cy + a][cx] - s[cy - a][cx]);
-        }
-#pragma unroll
-        for (int a = 1; a <= 2; ++a)
-#pragma unroll
-            for (int b = 1; b <= 2; ++b) {   // off-axis classes (a,b)
-                const real d1 = s[cy + b][cx + a] - s[cy - b][cx - a];   // (a,b) - (-a,-b)
-                const real d2 = s[cy - b][cx + a] - s[cy + b][cx - a];   // (a,-b) - (-a,b)
-                const real p = (real)p25(a * a + b * b);
-                ax += (p * (real)a) * (d1 + d2);
-                ay += (p * (real)b) * (d1 - d2);
-            }
-        sx = ax;
-        sy = ay;
+        vq25<float>([&](int dy, int dx) { return s[cy + dy][cx + dx]; }, p25f, sx, sy);
     }
 }
+
 
 // Total force on species k at the staged node (cx, cy): Eq. (8) + Eq. (9) + rho_k g.
 template <typename real, int SHv>
 __device__ __forceinline__ void force_at(const Lat<real> &L, const real (*srho)[SHv][SW], const real (*spsi)[SHv][SW],
                                          int k, int cx, int cy, real &Fx, real &Fy)
 {
-    real s1x, s1y, s2x, s2y, s3x, s3y;
-    q9_sum<real>(spsi[k], cx, cy, s1x, s1y);
-    q25_sum<real>(spsi[k], cx, cy, s2x, s2y);
-    q9_sum<real>(srho[1 - k], cx, cy, s3x, s3y);
     const real psi = spsi[k][cy][cx], rho = srho[k][cy][cx];
-    const real G1 = L.G1, G2 = L.G2, GAB = L.GAB;
-    Fx = -G1 * psi * s1x - G2 * psi * s2x - GAB * rho * s3x + rho * L.g[0];
-    Fy = -G1 * psi * s1y - G2 * psi * s2y - GAB * rho * s3y + rho * L.g[1];
+    if constexpr (kOffset<real>) {
+        // FP32: the two psi sums as one stencil with combined weights
+        float msx, msy, s3x, s3y;
+        const float(*sp)[SW] = spsi[k];
+        vq25c<float>([&](int dy, int dx) { return sp[cy + dy][cx + dx]; }, L.cw, p25f, msx, msy);
+        q9_sum<real>(srho[1 - k], cx, cy, s3x, s3y);
+        vforce<float>(psi, rho, msx, msy, s3x, s3y, L.GAB, L.g[0], L.g[1], Fx, Fy);
+    } else {
+        real s1x, s1y, s2x, s2y, s3x, s3y;
+        q9_sum<real>(spsi[k], cx, cy, s1x, s1y);
+        q25_sum<real>(spsi[k], cx, cy, s2x, s2y);
+        q9_sum<real>(srho[1 - k], cx, cy, s3x, s3y);
+        const real G1 = L.G1, G2 = L.G2, GAB = L.GAB;
+        Fx = -G1 * psi * s1x - G2 * psi * s2x - GAB * rho * s3x + rho * L.g[0];
+        Fy = -G1 * psi * s1y - G2 * psi * s2y - GAB * rho * s3y + rho * L.g[1];
+    }
 }
 
 // The staged density and psi tiles of the species as one [row][col] plane
@@ -232,6 +229,12 @@ struct SplitStage {
     __device__ __forceinline__ real density_step(int k, int cx, int cy) const
     {
         return srho[k][cy][cx] - srho[k][cy + EY][cx + EX];
+    }
+    // both species' densities at the staged node (cx + EX, cy + EY)
+    template <int EX, int EY>
+    __device__ __forceinline__ Sp<real> dest(int cx, int cy) const
+    {
+        return {srho[0][cy + EY][cx + EX], srho[1][cy + EY][cx + EX]};
     }
 };
 
@@ -265,13 +268,8 @@ __device__ __forceinline__ real collide_dir(real f, real rho, real ux, real uy, 
     const real w = (real)w9(I);
     const real eu = edot<real, EX, EY>(ux, uy);
     const real C = aw * (guo_comp<real, EX>(ux, eu) * Fx + guo_comp<real, EY>(uy, eu) * Fy);
-    if constexpr (!kOffset<real>) {
-        const real feq = w * rho * ((real)1 + (real)3 * eu + (real)4.5 * eu * eu - (real)1.5 * uu);
-        return f - om * (f - feq) + C;
-    } else {
-        const real geq = (w * rho) * ((real)3 * eu + (real)4.5 * eu * eu - (real)1.5 * uu);
-        return f - om * (f - geq) + C;
-    }
+    const real feq = w * rho * ((real)1 + (real)3 * eu + (real)4.5 * eu * eu - (real)1.5 * uu);
+    return f - om * (f - feq) + C;
 }
 
 // Store the post-collision value of direction I of species k at x + e_i
@@ -285,7 +283,7 @@ __device__ __forceinline__ void push_dir(const Lat<real> &L, real *__restrict__ 
     if constexpr (kOffset<real> && I != 0) {
         // the next step's reference at the destination is its density now
         if (kInner || !(EY != 0 && L.walls && (y + EY < 0 || y + EY >= L.ny)))
-            v += (real)w9(I) * sg.template density_step<EX, EY>(k, cx, cy);
+            v = cfma((float)w9(I), sg.template density_step<EX, EY>(k, cx, cy), v);
     }
     if constexpr (kInner) {
         // node and destination inside the lattice: a constant offset
@@ -313,50 +311,18 @@ __device__ __forceinline__ void push_dir(const Lat<real> &L, real *__restrict__ 
     }
 }
 
-// FP32 per-species constants of the collision shared by all directions.
-template <typename real>
-struct SpeciesTerms {
-    real uF[2];        // u^eq . F_k
-    real wr[2][3];     // w(|e|^2) rho_k
-    real aw3[2][3];    // 3 (1 - omega_k/2) w(|e|^2)
-    real dg[2];        // sum_i of the offsets from rho_k: minus the rounding of rho_k
-};
-
-// Collision and push of direction I of both species, fI[k] the node's
-// population (FP32: its offset) of that direction; sg the staged densities.
+// Collision and push of direction I of both species (FP64), fk the node's
+// populations; sg the staged densities.
 template <typename real, int I, bool kInner, class Stage>
 __device__ __forceinline__ void collide_push_dir(const Lat<real> &L, real *__restrict__ fn, const Stage &sg,
-                                                 const real (&fI)[2], const real (&rho)[2], real ux, real uy, real uu,
-                                                 const real (&F)[2][2], const SpeciesTerms<real> &st, int x, int y,
-                                                 int cx, int cy)
+                                                 const real (&fk)[2][9], const real (&rho)[2], real ux, real uy,
+                                                 real uu, const real (&F)[2][2], int x, int y, int cx, int cy)
 {
-    if constexpr (!kOffset<real>) {
-        (void)st;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const real v = collide_dir<real, I>(fI[k], rho[k], ux, uy, uu, F[k][0], F[k][1], L.omega[k],
-                                                L.aw[k][cls9(I)]);
-            push_dir<real, I, kInner>(L, fn, sg, k, x, y, cx, cy, v);
-        }
-    } else {
-        // Eq. (2) less w rho (the node's own density is the offset), and Eq. (5)
-        // rewritten as 3 (1 - 1/2tau) w [(e.F)(1 + 3 e.u) - u.F]; the direction
-        // terms are shared by both species.
-        constexpr int EX = ex9(I), EY = ey9(I), C = cls9(I);
-        const real eu = edot<real, EX, EY>(ux, uy);
-        const real q = (real)4.5 * eu * eu + ((real)3 * eu - (real)1.5 * uu);
-        const real tt = (real)1 + (real)3 * eu;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const real eF = edot<real, EX, EY>(F[k][0], F[k][1]);
-            const real Cg = st.aw3[k][C] * (eF * tt - st.uF[k]);
-            // the equilibrium carries the node's exact mass: its offsets from the
-            // rounded rho_k sum to dg, like the populations' do
-            const real geq = st.wr[k][C] * q + (real)w9(I) * st.dg[k];
-            const real f = fI[k];
-            const real v = (f + L.omega[k] * (geq - f)) + Cg;
-            push_dir<real, I, kInner>(L, fn, sg, k, x, y, cx, cy, v);
-        }
+    for (int k = 0; k < 2; ++k) {
+        const real v = collide_dir<real, I>(fk[k][I], rho[k], ux, uy, uu, F[k][0], F[k][1], L.omega[k],
+                                            L.aw[k][cls9(I)]);
+        push_dir<real, I, kInner>(L, fn, sg, k, x, y, cx, cy, v);
     }
 }
 
@@ -369,9 +335,7 @@ __device__ __forceinline__ void first_moment(const real (&f)[9], real &jx, real 
         jx = ((((f[1] - f[3]) + f[5]) - f[6]) - f[7]) + f[8];
         jy = ((((f[2] - f[4]) + f[5]) + f[6]) - f[7]) - f[8];
     } else {
-        const real d57 = f[5] - f[7], d86 = f[8] - f[6];
-        jx = (f[1] - f[3]) + (d57 + d86);
-        jy = (f[2] - f[4]) + (d57 - d86);
+        vfirst<float>(f, jx, jy);
     }
 }
 
@@ -381,7 +345,7 @@ __device__ __forceinline__ real zeroth_moment(const real (&f)[9])
     if constexpr (!kOffset<real>) {
         return (((((((f[0] + f[1]) + f[2]) + f[3]) + f[4]) + f[5]) + f[6]) + f[7]) + f[8];
     } else {
-        return f[0] + (((f[1] + f[3]) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8])));
+        return vzeroth<float>(f);
     }
 }
 
@@ -458,8 +422,8 @@ __device__ __forceinline__ void collide_tile(const Lat<real> *__restrict__ lats,
     const Lat<real> &G = lats[t.x];
     const int tid = threadIdx.y * TX + threadIdx.x;
     static_assert(sizeof(Lat<real>) % 4 == 0, "descriptor copied as 32-bit words");
-    if (tid < (int)(sizeof(Lat<real>) / 4))
-        reinterpret_cast<uint32_t *>(&sm.L)[tid] = reinterpret_cast<const uint32_t *>(&G)[tid];
+    for (int i = tid; i < (int)(sizeof(Lat<real>) / 4); i += TX * TYv)
+        reinterpret_cast<uint32_t *>(&sm.L)[i] = reinterpret_cast<const uint32_t *>(&G)[i];
     const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
     const bool valid = x < G.nx && y < G.ny;
     // issue the population loads first so their latency overlaps the staging
@@ -539,16 +503,17 @@ template <typename real>
 __device__ __forceinline__ void node_moments(const real *__restrict__ box, int box_plane, const real (&rho)[2],
                                              const real (&Rn)[2], NodeMoments<real> &nm)
 {
+    static_assert(kOffset<real>, "the box form is FP32 only");
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        real f[9];
+        float f[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = box[(k * 9 + i) * box_plane];
-        first_moment<real>(f, nm.j[k][0], nm.j[k][1]);
-        nm.delta[k] = rho[k] - Rn[k];
+        vfirst<float>(f, nm.j[k][0], nm.j[k][1]);
+        nm.delta[k] = vsub(rho[k], Rn[k]);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] -= (real)w9(i) * nm.delta[k];
-        nm.dg[k] = zeroth_moment<real>(f);
+        for (int i = 0; i < 9; ++i) f[i] = cfma(-(float)w9(i), nm.delta[k], f[i]);
+        nm.dg[k] = vzeroth<float>(f);
     }
 }
 
@@ -622,99 +587,137 @@ __device__ __forceinline__ void shift_collide_site(const Lat<real> &L, real *__r
 // species k, read again where it is used with the same density offset
 // applied, which keeps 18 registers free; fk is then not used, and the
 // force-free moments come precomputed in *pre (node_moments).
+// The FP32 node collision: half-force momenta (Eq. 6), the offsets from the
+// node's current density, u^eq and the terms shared by the directions, then
+// the collision of each direction of both species and its push.
+template <bool kInner, bool kBox, class Stage>
+__device__ __forceinline__ void collide_site_off(const Lat<float> &L, float *__restrict__ fn, const Stage &sg,
+                                                 float (&fk)[2][9], const float (&Rn)[2], int x, int y, int cx, int cy,
+                                                 const float *__restrict__ box, int box_plane,
+                                                 const NodeMoments<float> *pre)
+{
+    float F[2][2], rho[2], m[2][2], dg[2], delta[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        sg.force(L, k, cx, cy, F[k][0], F[k][1]);
+        rho[k] = sg.density(k, cy, cx);
+        float jx, jy;
+        if constexpr (kBox) {
+            jx = pre->j[k][0];
+            jy = pre->j[k][1];
+            delta[k] = pre->delta[k];
+            dg[k] = pre->dg[k];
+        } else {
+            float(&f)[9] = fk[k];
+            vfirst<float>(f, jx, jy);   // the reference density adds no momentum
+            // offsets from the node's current density: h_i - w_i (rho - R).
+            // rho - R is formed from the rounded density itself (exact: the two
+            // are close), so f = h + w R is kept exactly whatever rho rounded to;
+            // with sum_i h_i instead, density changes below half an ulp of R
+            // would be dropped at every step and mass would drift.
+            delta[k] = vsub(rho[k], Rn[k]);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = cfma(-(float)w9(i), delta[k], f[i]);
+            dg[k] = vzeroth<float>(f);
+        }
+        m[k][0] = cfma(0.5f, F[k][0], jx);   // Eq. (6), half force
+        m[k][1] = cfma(0.5f, F[k][1], jy);
+    }
+    OffTerms<float> t;
+    off_terms<float>(L.omega[0], L.omega[1], rho, m, F, dg, t);
+    // the lattice constants of the collision, read once: stores to the
+    // populations may alias shared memory as far as the compiler knows
+    const float om[2] = {L.omega[0], L.omega[1]};
+    const float aw3[2][3] = {{L.aw3[0][0], L.aw3[0][1], L.aw3[0][2]}, {L.aw3[1][0], L.aw3[1][1], L.aw3[1][2]}};
+    const size_t plane = L.plane;
+    const int pitch = L.pitch;
+    float *node = fn + ((size_t)y * pitch + x);
+    // the population of direction I of species k, as the moments saw it
+    auto pop = [&](int k, int I) -> float {
+        if constexpr (kBox) return cfma(-(float)w9(I), delta[k], box[(k * 9 + I) * box_plane]);
+        else return fk[k][I];
+    };
+    Sp<float> dest{0.f, 0.f};
+    auto dir = [&](auto Ic) {
+        constexpr int I = decltype(Ic)::value;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            float v = off_collide<I, float>(t, k, om[k], aw3[k][cls9(I)], pop(k, I));
+            if constexpr (kInner) {
+                // destination inside the lattice: re-reference from rho(x) to
+                // rho(x + e_i), the reference the next step reads there, and
+                // store at a constant offset
+                constexpr int EX = ex9(I), EY = ey9(I);
+                if constexpr (I != 0) {
+                    if (k == 0) dest = sg.template dest<EX, EY>(cx, cy);
+                    v = cfma((float)w9(I), vsub(rho[k], k ? dest.b : dest.a), v);
+                }
+                node[(size_t)(k * 9 + I) * plane + (EY * pitch + EX)] = v;
+            } else {
+                push_dir<float, I, kInner>(L, fn, sg, k, x, y, cx, cy, v);
+            }
+        }
+    };
+    dir(std::integral_constant<int, 0>{});
+    dir(std::integral_constant<int, 1>{});
+    dir(std::integral_constant<int, 2>{});
+    dir(std::integral_constant<int, 3>{});
+    dir(std::integral_constant<int, 4>{});
+    dir(std::integral_constant<int, 5>{});
+    dir(std::integral_constant<int, 6>{});
+    dir(std::integral_constant<int, 7>{});
+    dir(std::integral_constant<int, 8>{});
+}
+
+// Force, moments, u^eq, collision and push of the node (x, y), staged at
+// (cx, cy).  Its populations are fk (updated in place), or with kBox (FP32)
+// the shared-memory box: box[(k * 9 + i) * box_plane] is population i of
+// species k, read again where it is used with the same density offset
+// applied, which keeps 18 registers free; fk is then not used, and the
+// force-free moments come precomputed in *pre (node_moments).
 template <typename real, bool kInner, bool kBox, class Stage>
 __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const Stage &sg,
                                              real (&fk)[2][9], const real (&Rn)[2], int x, int y, int cx, int cy,
                                              const real *__restrict__ box, int box_plane, const NodeMoments<real> *pre)
 {
     static_assert(!kBox || kOffset<real>, "the box form is FP32 only");
-    if constexpr (!kOffset<real>) {
+    if constexpr (kOffset<real>) {
+        collide_site_off<kInner, kBox>(L, fn, sg, fk, Rn, x, y, cx, cy, box, box_plane, pre);
+    } else {
+        (void)Rn;
+        (void)box;
+        (void)box_plane;
+        (void)pre;
         if (L.forcing == 1) {   // the original model (Eq. 4), a block-uniform branch
             shift_collide_site<real, kInner>(L, fn, sg, fk, x, y, cx, cy);
             return;
         }
-    }
-    real F[2][2], rho[2], m[2][2], dg[2] = {(real)0, (real)0}, delta[2] = {(real)0, (real)0};
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        sg.force(L, k, cx, cy, F[k][0], F[k][1]);
-        rho[k] = sg.density(k, cy, cx);
-        if constexpr (kBox) {
-            m[k][0] = pre->j[k][0] + (real)0.5 * F[k][0];   // Eq. (6), half force
-            m[k][1] = pre->j[k][1] + (real)0.5 * F[k][1];
-            delta[k] = pre->delta[k];
-            dg[k] = pre->dg[k];
-            continue;
-        }
-        real(&f)[9] = fk[k];
-        real jx, jy;
-        first_moment<real>(f, jx, jy);     // FP32: the reference density adds no momentum
-        m[k][0] = jx + (real)0.5 * F[k][0];   // Eq. (6), half force
-        m[k][1] = jy + (real)0.5 * F[k][1];
-        if constexpr (kOffset<real>) {
-            // offsets from the node's current density: h_i - w_i (rho - R).
-            // rho - R is formed from the rounded density itself (exact: the two
-            // are close), so f = h + w R is kept exactly whatever rho rounded to;
-            // with sum_i h_i instead, density changes below half an ulp of R
-            // would be dropped at every step and mass would drift.
-            delta[k] = rho[k] - Rn[k];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] -= (real)w9(i) * delta[k];
-            dg[k] = zeroth_moment<real>(f);
-        }
-    }
-    // common velocity, Eq. (3)
-    const real om0 = L.omega[0], om1 = L.omega[1];
-    const real den = om0 * rho[0] + om1 * rho[1];
-    const real ux = (om0 * m[0][0] + om1 * m[1][0]) / den;
-    const real uy = (om0 * m[0][1] + om1 * m[1][1]) / den;
-    const real uu = ux * ux + uy * uy;
-    SpeciesTerms<real> st;
-    if constexpr (kOffset<real>) {
+        real F[2][2], rho[2], m[2][2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            st.dg[k] = dg[k];
-            st.uF[k] = ux * F[k][0] + uy * F[k][1];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                st.wr[k][c] = (real)w9(c == 0 ? 0 : (c == 1 ? 1 : 5)) * rho[k];
-                st.aw3[k][c] = (real)3 * L.aw[k][c];
-            }
+            sg.force(L, k, cx, cy, F[k][0], F[k][1]);
+            rho[k] = sg.density(k, cy, cx);
+            real jx, jy;
+            first_moment<real>(fk[k], jx, jy);
+            m[k][0] = jx + (real)0.5 * F[k][0];   // Eq. (6), half force
+            m[k][1] = jy + (real)0.5 * F[k][1];
         }
+        // common velocity, Eq. (3)
+        const real om0 = L.omega[0], om1 = L.omega[1];
+        const real den = om0 * rho[0] + om1 * rho[1];
+        const real ux = (om0 * m[0][0] + om1 * m[1][0]) / den;
+        const real uy = (om0 * m[0][1] + om1 * m[1][1]) / den;
+        const real uu = ux * ux + uy * uy;
+        collide_push_dir<real, 0, kInner>(L, fn, sg, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+        collide_push_dir<real, 1, kInner>(L, fn, sg, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+        collide_push_dir<real, 2, kInner>(L, fn, sg, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+        collide_push_dir<real, 3, kInner>(L, fn, sg, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+        collide_push_dir<real, 4, kInner>(L, fn, sg, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+        collide_push_dir<real, 5, kInner>(L, fn, sg, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+        collide_push_dir<real, 6, kInner>(L, fn, sg, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+        collide_push_dir<real, 7, kInner>(L, fn, sg, fk, rho, ux, uy, uu, F, x, y, cx, cy);
+        collide_push_dir<real, 8, kInner>(L, fn, sg, fk, rho, ux, uy, uu, F, x, y, cx, cy);
     }
-
-    // the population of direction I of both species, as the moments saw it
-    auto dir_pops = [&](int I, real(&fI)[2]) {
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            if constexpr (kBox) {
-                real h = box[(k * 9 + I) * box_plane];
-                h -= (real)w9(I) * delta[k];
-                fI[k] = h;
-            } else {
-                fI[k] = fk[k][I];
-            }
-        }
-    };
-    real fI[2];
-    dir_pops(0, fI);
-    collide_push_dir<real, 0, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    dir_pops(1, fI);
-    collide_push_dir<real, 1, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    dir_pops(2, fI);
-    collide_push_dir<real, 2, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    dir_pops(3, fI);
-    collide_push_dir<real, 3, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    dir_pops(4, fI);
-    collide_push_dir<real, 4, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    dir_pops(5, fI);
-    collide_push_dir<real, 5, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    dir_pops(6, fI);
-    collide_push_dir<real, 6, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    dir_pops(7, fI);
-    collide_push_dir<real, 7, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
-    dir_pops(8, fI);
-    collide_push_dir<real, 8, kInner>(L, fn, sg, fI, rho, ux, uy, uu, F, st, x, y, cx, cy);
 }
 
 // ---- one-pass step ------------------------------------------------------------
@@ -789,8 +792,8 @@ __device__ __forceinline__ void fused_tile(const Lat<real> *__restrict__ lats, i
     constexpr int SHv = TYv + 2 * HALO;
     const Lat<real> &G = lats[t.x];
     const int tid = threadIdx.y * TX + threadIdx.x;
-    if (tid < (int)(sizeof(Lat<real>) / 4))
-        reinterpret_cast<uint32_t *>(&sm.L)[tid] = reinterpret_cast<const uint32_t *>(&G)[tid];
+    for (int i = tid; i < (int)(sizeof(Lat<real>) / 4); i += TX * TYv)
+        reinterpret_cast<uint32_t *>(&sm.L)[i] = reinterpret_cast<const uint32_t *>(&G)[i];
     const int nx = G.nx, ny = G.ny;
     const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
     const bool valid = x < nx && y < ny;

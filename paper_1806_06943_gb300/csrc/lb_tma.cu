@@ -1,11 +1,11 @@
 // lb_tma.cu -- the FP32 one-pass time step with each tile's populations and
 // reference densities, halo included, brought into shared memory by the
 // tensor memory accelerator (cp.async.bulk.tensor, completion on an mbarrier)
-// instead of per-thread loads.  Same arithmetic as fused_tile in the same
-// order, so the results are the same bit for bit: the densities of the staged
-// nodes are the sums of Eq. (6) over the boxed populations, then the forces
-// of Eqs. (8), (9), the collision of Eqs. (1), (2), (5) and the push
-// streaming of collide_site.
+// instead of per-thread loads.  The explicit FP32 arithmetic of lb_vops.cuh,
+// in the same order as fused_tile, so the results are the same bit for bit:
+// the densities of the staged nodes are the sums of Eq. (6) over the boxed
+// populations, then the forces of Eqs. (8), (9), the collision of Eqs. (1),
+// (2), (5) and the push streaming of collide_site.
 //
 // Box of a tile (x0, y0) of 32 x TY nodes: columns x0 - 4 .. x0 + 35 (the
 // D2Q25 halo needs 2; 4 keep the x offset a multiple of 16 bytes), rows
@@ -105,63 +105,6 @@ struct PairSmem {
     Lat<float> L;   // descriptor copy: stores to the populations cannot alias it
 };
 
-// q9_sum (FP32) of both components of a pair plane: the same differences of
-// opposite neighbours and the same expressions, per species.
-template <int SHv>
-__device__ __forceinline__ void q9_pair(const float2 (*s)[SW], int cx, int cy, float (&sx)[2], float (&sy)[2])
-{
-    const float W1 = (float)(1.0 / 9.0), W2 = (float)(1.0 / 36.0);
-    const float2 e = s[cy][cx + 1], w = s[cy][cx - 1], n = s[cy + 1][cx], so = s[cy - 1][cx];
-    const float2 ne = s[cy + 1][cx + 1], sw = s[cy - 1][cx - 1], se = s[cy - 1][cx + 1], nw = s[cy + 1][cx - 1];
-    {
-        const float dE = e.x - w.x, dN = n.x - so.x, d1 = ne.x - sw.x, d2 = se.x - nw.x;
-        sx[0] = W1 * dE + W2 * (d1 + d2);
-        sy[0] = W1 * dN + W2 * (d1 - d2);
-    }
-    {
-        const float dE = e.y - w.y, dN = n.y - so.y, d1 = ne.y - sw.y, d2 = se.y - nw.y;
-        sx[1] = W1 * dE + W2 * (d1 + d2);
-        sy[1] = W1 * dN + W2 * (d1 - d2);
-    }
-}
-
-// q25_sum (FP32) of both components of a pair plane, same classes and order.
-template <int SHv>
-__device__ __forceinline__ void q25_pair(const float2 (*s)[SW], int cx, int cy, float (&sx)[2], float (&sy)[2])
-{
-    float ax[2] = {0.f, 0.f}, ay[2] = {0.f, 0.f};
-#pragma unroll
-    for (int a = 1; a <= 2; ++a) {   // axis classes (a,0) and (0,a)
-        const float p = (float)(p25(a * a) * a);
-        const float2 xp = s[cy][cx + a], xm = s[cy][cx - a], yp = s[cy + a][cx], ym = s[cy - a][cx];
-        ax[0] += p * (xp.x - xm.x);
-        ay[0] += p * (yp.x - ym.x);
-        ax[1] += p * (xp.y - xm.y);
-        ay[1] += p * (yp.y - ym.y);
-    }
-#pragma unroll
-    for (int a = 1; a <= 2; ++a)
-#pragma unroll
-        for (int b = 1; b <= 2; ++b) {   // off-axis classes (a,b)
-            const float2 pp = s[cy + b][cx + a], mm = s[cy - b][cx - a], pm = s[cy - b][cx + a], mp = s[cy + b][cx - a];
-            const float p = (float)p25(a * a + b * b);
-            {
-                const float d1 = pp.x - mm.x, d2 = pm.x - mp.x;
-                ax[0] += (p * (float)a) * (d1 + d2);
-                ay[0] += (p * (float)b) * (d1 - d2);
-            }
-            {
-                const float d1 = pp.y - mm.y, d2 = pm.y - mp.y;
-                ax[1] += (p * (float)a) * (d1 + d2);
-                ay[1] += (p * (float)b) * (d1 - d2);
-            }
-        }
-    sx[0] = ax[0];
-    sy[0] = ay[0];
-    sx[1] = ax[1];
-    sy[1] = ay[1];
-}
-
 // The pair planes as collide_site reads them (the interface of SplitStage):
 // species 0's force and density step are formed together with species 1's,
 // which are kept for the call that follows for species 1.
@@ -175,7 +118,7 @@ struct PairStage {
         const float2 v = sr[cy][cx];
         return k ? v.y : v.x;
     }
-    // Eq. (8) + Eq. (9) + rho_k g, as force_at
+    // Eq. (8) + Eq. (9) + rho_k g, as force_at (the same operations per species)
     __device__ __forceinline__ void force(const Lat<float> &L, int k, int cx, int cy, float &Fx, float &Fy) const
     {
         if (k) {
@@ -183,24 +126,34 @@ struct PairStage {
             Fy = F1y;
             return;
         }
-        float s1x[2], s1y[2], s2x[2], s2y[2], s3x[2], s3y[2];
-        q9_pair<SHv>(sp, cx, cy, s1x, s1y);
-        q25_pair<SHv>(sp, cx, cy, s2x, s2y);
-        q9_pair<SHv>(sr, cx, cy, s3x, s3y);   // component j: sums over species j's density
+        auto at_psi = [&](int dy, int dx) -> Sp<float> {
+            const float2 v = sp[cy + dy][cx + dx];
+            return {v.x, v.y};
+        };
+        auto at_rho = [&](int dy, int dx) -> Sp<float> {
+            const float2 v = sr[cy + dy][cx + dx];
+            return {v.x, v.y};
+        };
+        Sp<float> msx, msy, s3x, s3y;
+        vq25c<Sp<float>>(at_psi, L.cw, p25f, msx, msy);
+        vq9<Sp<float>>(at_rho, s3x, s3y);   // component j: sums over species j's density
         const float2 psi = sp[cy][cx], rho = sr[cy][cx];
-        const float G1 = L.G1, G2 = L.G2, GAB = L.GAB;
-        Fx = -G1 * psi.x * s1x[0] - G2 * psi.x * s2x[0] - GAB * rho.x * s3x[1] + rho.x * L.g[0];
-        Fy = -G1 * psi.x * s1y[0] - G2 * psi.x * s2y[0] - GAB * rho.x * s3y[1] + rho.x * L.g[1];
-        F1x = -G1 * psi.y * s1x[1] - G2 * psi.y * s2x[1] - GAB * rho.y * s3x[0] + rho.y * L.g[0];
-        F1y = -G1 * psi.y * s1y[1] - G2 * psi.y * s2y[1] - GAB * rho.y * s3y[0] + rho.y * L.g[1];
+        vforce<float>(psi.x, rho.x, msx.a, msy.a, s3x.b, s3y.b, L.GAB, L.g[0], L.g[1], Fx, Fy);
+        vforce<float>(psi.y, rho.y, msx.b, msy.b, s3x.a, s3y.a, L.GAB, L.g[0], L.g[1], F1x, F1y);
+    }
+    template <int EX, int EY>
+    __device__ __forceinline__ Sp<float> dest(int cx, int cy) const
+    {
+        const float2 v = sr[cy + EY][cx + EX];
+        return {v.x, v.y};
     }
     template <int EX, int EY>
     __device__ __forceinline__ float density_step(int k, int cx, int cy) const
     {
         if (k) return d1;
         const float2 a = sr[cy][cx], b = sr[cy + EY][cx + EX];
-        d1 = a.y - b.y;
-        return a.x - b.x;
+        d1 = vsub(a.y, b.y);
+        return vsub(a.x, b.x);
     }
 };
 
@@ -241,16 +194,15 @@ __device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ la
     constexpr int SHv = TYv + 2 * HALO, H = SHv, W = kTmaBoxW;
     const Lat<float> &G = lats[t.x];
     const int tid = threadIdx.y * TX + threadIdx.x;
-    if (tid < (int)(sizeof(Lat<float>) / 4))
-        reinterpret_cast<uint32_t *>(&sm.L)[tid] = reinterpret_cast<const uint32_t *>(&G)[tid];
+    for (int i = tid; i < (int)(sizeof(Lat<float>) / 4); i += TX * TYv)
+        reinterpret_cast<uint32_t *>(&sm.L)[i] = reinterpret_cast<const uint32_t *>(&G)[i];
     // staged slot (sx, sy) is box column sx + 2, row sy; the same sums as
     // node_density
     auto slot_density = [&](int k, int sx, int sy) {
         float v[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) v[i] = pop[((k * 9 + i) * H + sy) * W + sx + 2];
-        const float r = zeroth_moment<float>(v);
-        return ref[(k * H + sy) * W + sx + 2] + r;
+        return vadd(ref[(k * H + sy) * W + sx + 2], vzeroth<float>(v));
     };
     constexpr int kRing = 4 * SW + 4 * TYv;
     for (int h = tid; h < kRing; h += TX * TYv) {
@@ -273,7 +225,7 @@ __device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ la
 #pragma unroll
         for (int i = 0; i < 9; ++i) v[i] = own[(k * 9 + i) * H * W];
         Rn[k] = ref[(k * H + cy) * W + cx + 2];
-        const float r = Rn[k] + zeroth_moment<float>(v);
+        const float r = vadd(Rn[k], vzeroth<float>(v));
         G.rho[parity ^ 1][(size_t)k * G.plane + c] = r;
         rn[k] = r;
     }

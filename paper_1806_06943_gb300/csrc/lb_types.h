@@ -47,6 +47,8 @@ struct Lat {
     real omega[2];       // 1 / tau_k
     real tau[2];         // tau_k (the velocity shift tau_k F_k / rho_k of Eq. 4)
     real aw[2][3];       // (1 - omega_k / 2) * w(|e|^2) for |e|^2 = 0, 1, 2
+    real aw3[2][3];      // 3 aw, rounded in the compute precision (the FP32 Guo term)
+    real cw[3];          // FP32: -(G1 w + G2 p) for |e|^2 = 1, 2 and -G2 (Eq. 8; vq25c)
     real G1, G2, GAB;
     real g[2];
     real wall_rho[2];
