@@ -207,11 +207,11 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-KERNEL_SOURCES = ("lb_kernels.cuh", "lb_tma.cu")
+KERNEL_SOURCES = ("lb_kernels.cuh", "lb_vops.cuh", "lb_tma.cu")
 
 
 def kernel_source_sha1() -> str:
-    """SHA-1 over the kernel sources (lb_kernels.cuh, then lb_tma.cu)."""
+    """SHA-1 over the kernel sources (lb_kernels.cuh, lb_vops.cuh, then lb_tma.cu)."""
     import hashlib
     h = hashlib.sha1()
     for name in KERNEL_SOURCES:
