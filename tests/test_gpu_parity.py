@@ -120,6 +120,7 @@ def test_fp32_offset_c1_droplet(oracle_mod, lbmod):
     o, g = run_pair(oracle_mod, lbmod, rho, 2000, precision=1, **C6)
     fo, fg = o.fields(), g.fields()
     er, eu = nrel(fg["rho"], fo["rho"]), nrel(fg["ubar"], fo["ubar"])
+    print(f"C1 FP32 2000 steps: rho {er:.2e} u {eu:.2e}")
     assert er <= 1e-5, er
     assert eu <= 1e-5, eu
     oo = o.observables((32, 32, 12))
@@ -145,8 +146,10 @@ def test_fp32_offset_channel_mu_r(oracle_mod, lbmod):
     oo, og = o.observables(), g.observables()
     assert abs(og["mu_r"] - oo["mu_r"]) <= 1e-3 * abs(oo["mu_r"])
     fo, fg = o.fields(), g.fields()
-    assert nrel(fg["rho"], fo["rho"]) <= 2e-5
-    assert nrel(fg["ubar"], fo["ubar"]) <= 5e-5
+    er, eu = nrel(fg["rho"], fo["rho"]), nrel(fg["ubar"], fo["ubar"])
+    print(f"channel 96x48 FP32 1500 steps: rho {er:.2e} u {eu:.2e} mu_r {abs(og['mu_r'] - oo['mu_r']) / abs(oo['mu_r']):.2e}")
+    assert er <= 2e-5
+    assert eu <= 5e-5
 
 
 def test_batch_matches_oracle_per_lattice(oracle_mod, lbmod):
