@@ -112,7 +112,7 @@ def test_channel_emulsion_512x128_5000_steps(lbmod):
     central differences of the FP64 GPU forward (each one tied to the
     oracle's arithmetic) at 1e-4.  The FP32 forward (FP64 adjoint linearised
     at the FP32 trajectory) is held to its observable tolerance: mu_r within
-    1e-4 (measured 3e-5) and the gradient within 2e-3 (measured 1.1e-3).  Its
+    1e-4 (measured 2e-5) and the gradient within 1e-3 (measured 3.1e-4).  Its
     trajectory carries the FP32 rounding bias of a body-forced flow (c17),
     and the gradient of this dense emulsion is itself sensitive: a 2e-5
     change of the continuous phase's viscosity moves the FP64 gradient by
@@ -134,7 +134,7 @@ def test_channel_emulsion_512x128_5000_steps(lbmod):
     L32.set_fields(rho)
     J32, dJ32 = L32.grad(5000, 250, lbmod.LB_OBJ_MU_R)      # FP32 forward, FP64 adjoint
     assert abs(J32 - J) <= 1e-4 * abs(J)
-    assert np.max(np.abs(dJ32 - dJ) / np.abs(dJ)) <= 2e-3, (dJ32, dJ)
+    assert np.max(np.abs(dJ32 - dJ) / np.abs(dJ)) <= 1e-3, (dJ32, dJ)
     g = np.zeros(5)
     for a in range(5):
         tp, tm = theta.copy(), theta.copy()

@@ -133,9 +133,9 @@ def test_fp32_offset_c1_droplet(oracle_mod, lbmod):
 def test_fp32_offset_channel_mu_r(oracle_mod, lbmod):
     """Body-forced channel with non-wetting walls (g = 1e-5, ten times the
     emulsion workloads' forcing): mu_r of FP32 within 1e-3 of the oracle
-    (measured 3.5e-6).  The FP32 velocity carries the systematic rounding bias
+    (measured 3.2e-6).  The FP32 velocity carries the systematic rounding bias
     of the momentum-carrying terms under a body force, which grows with g t:
-    measured 4.1e-5 on u and 1.1e-5 on rho (the drops advect with the biased
+    measured 3.5e-5 on u and 9.4e-6 on rho (the drops advect with the biased
     flow), while an FP64 run with its initial densities perturbed by 1e-7
     moves by only 2.9e-7 and 1.3e-7, so the excess is FP32 arithmetic, not
     amplification; held to 5e-5 (u) and 2e-5 (rho)."""
