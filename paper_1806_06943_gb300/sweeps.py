@@ -147,15 +147,16 @@ def body_force(F_bar: float, L: int, tau_c: float = 1.0, rho_b: float = W.MAJORI
     return 8.0 * F_bar * mu * mu / (rho_b * rho_b * L ** 3)
 
 
-def droplet_array(L: int, n: int, R: float, seed: int) -> tuple[np.ndarray, float]:
+def droplet_array(L: int, n: int, R: float, seed: int, noise: float = W.NOISE) -> tuple[np.ndarray, float]:
     """n x n equal drops on a square lattice of spacing L / n in an L x L
     channel (walls in y), and the achieved area fraction; n = 0 gives the
-    droplet-free continuous phase."""
+    droplet-free continuous phase.  noise: amplitude of the seeded uniform
+    perturbation of the densities (0: the exact symmetric array)."""
     if n == 0:
-        return W.droplets(L, L, [], [], seed=seed, periodic=False), 0.0
+        return W.droplets(L, L, [], [], seed=seed, noise=noise, periodic=False), 0.0
     s = L / n
     centres = [((i + 0.5) * s, (j + 0.5) * s) for j in range(n) for i in range(n)]
-    rho = W.droplets(L, L, centres, [R] * len(centres), seed=seed, periodic=False)
+    rho = W.droplets(L, L, centres, [R] * len(centres), seed=seed, noise=noise, periodic=False)
     phi = float((rho[0] > 0.5 * (W.MAJORITY + W.MINORITY)).mean())
     return rho, phi
 
@@ -182,7 +183,7 @@ def count_drops(rho_a: np.ndarray, threshold: float = 0.5) -> int:
 
 def rheology(cases: list[dict], L: int = 220, n: int = 5, steps: int = 200000, window: int = 40000,
              sample_every: int = 2000, precision: int = lb.LB_FP32, seed: int = W.BASE_SEED + 12,
-             couplings=None) -> list[dict]:
+             couplings=None, noise: float = W.NOISE) -> list[dict]:
     """mu_r for each case dict(R, M, F_bar) (R = 0: no drops), all in one
     batch: L x L channel, fixed non-wetting wall densities, tau_B = 1.  The
     flow rate Q of every lattice is averaged over the last `window` steps;
@@ -198,7 +199,7 @@ def rheology(cases: list[dict], L: int = 220, n: int = 5, steps: int = 200000, w
         g = body_force(c["F_bar"], L)
         specs.append(dict(nx=L, ny=L, tau=(tau_for_ratio(c["M"]), 1.0), g=(g, 0.0), walls=1, wall_mode=1,
                           wall_rho=(W.MINORITY, W.MAJORITY), **couplings))
-        rho, phi = droplet_array(L, n if c["R"] > 0 else 0, c["R"], seed)
+        rho, phi = droplet_array(L, n if c["R"] > 0 else 0, c["R"], seed, noise=noise)
         fields.append(rho)
         phis.append(phi)
     b = lb.Batch(specs, precision=precision)
