@@ -65,19 +65,20 @@ def laplace_side(R: float) -> int:
 
 def tension_scan(G1: float, G2: float, g_ab_values, radii=(12.0, 18.0, 24.0, 42.0), steps: int = 20000,
                  tau=(1.0, 1.0), precision: int = lb.LB_FP32, seed: int = W.BASE_SEED + 11,
-                 init_width: float | None = None) -> list[dict]:
+                 init_width: float | None = None, noise: float = W.NOISE) -> list[dict]:
     """Laplace tests for every G_AB of g_ab_values at couplings (G1, G2), all
     in one batch; returns per G_AB: W (largest drop), gamma and the R^2 of the
     Laplace fit, and whether every drop stayed finite.  The drops start as
-    sharp disks, or with a tanh interface of width init_width."""
+    sharp disks, or with a tanh interface of width init_width, with the
+    seeded density noise of amplitude `noise`."""
     g_ab_values = [float(v) for v in g_ab_values]
     specs, fields, probes = [], [], []
     for gab in g_ab_values:
         for R in radii:
             n = laplace_side(R)
             specs.append(dict(nx=n, ny=n, tau=tau, G_AB=gab, G1=G1, G2=G2))
-            fields.append(W.droplet(n, n, R, seed=seed) if init_width is None
-                          else W.smooth_droplet(n, n, R, init_width, seed=seed))
+            fields.append(W.droplet(n, n, R, seed=seed, noise=noise) if init_width is None
+                          else W.smooth_droplet(n, n, R, init_width, seed=seed, noise=noise))
             probes.append((n / 2, n / 2, R))
     b = lb.Batch(specs, precision=precision)
     try:
