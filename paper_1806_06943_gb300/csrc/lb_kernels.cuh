@@ -165,28 +165,23 @@ __device__ __forceinline__ void q9_sum(const real (*s)[SW], int cx, int cy, real
     }
 }
 
-// sum_j p_j s(x + e_j) e_j over D2Q25.
-// FP64: raster order (dy outer, dx inner).  FP32: opposite-neighbour
-// differences grouped by |e_x|, |e_y| class.
+// sum_j p_j s(x + e_j) e_j over D2Q25 (FP64), in raster order (dy outer, dx
+// inner).  The FP32 step sums the psi terms with combined weights (vq25c).
 template <typename real>
 __device__ __forceinline__ void q25_sum(const real (*s)[SW], int cx, int cy, real &sx, real &sy)
 {
-    if constexpr (!kOffset<real>) {
-        sx = (real)0;
-        sy = (real)0;
+    static_assert(!kOffset<real>, "FP64 only");
+    sx = (real)0;
+    sy = (real)0;
 #pragma unroll
-        for (int j = 0; j < 25; ++j) {
-            const int dx = j % 5 - 2, dy = j / 5 - 2;
-            if (dx == 0 && dy == 0) continue;
-            const real pp = (real)p25(dx * dx + dy * dy) * s[cy + dy][cx + dx];
-            if (dx != 0) sx += pp * (real)dx;
-            if (dy != 0) sy += pp * (real)dy;
-        }
-    } else {
-        vq25<float>([&](int dy, int dx) { return s[cy + dy][cx + dx]; }, p25f, sx, sy);
+    for (int j = 0; j < 25; ++j) {
+        const int dx = j % 5 - 2, dy = j / 5 - 2;
+        if (dx == 0 && dy == 0) continue;
+        const real pp = (real)p25(dx * dx + dy * dy) * s[cy + dy][cx + dx];
+        if (dx != 0) sx += pp * (real)dx;
+        if (dy != 0) sy += pp * (real)dy;
     }
 }
-
 
 // Total force on species k at the staged node (cx, cy): Eq. (8) + Eq. (9) + rho_k g.
 template <typename real, int SHv>

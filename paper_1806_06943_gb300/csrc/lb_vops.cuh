@@ -75,32 +75,6 @@ __device__ __forceinline__ void vq9(const At &at, V &sx, V &sy)
     sy = cfma(W1, dN, cmul(W2, vsub(d1, d2)));
 }
 
-// sum_j p_j s(x + e_j) e_j over D2Q25: opposite-neighbour differences, the
-// axis classes (a,0), (0,a) first, then the off-axis classes (a,b).
-template <class V, class At, class Pf>
-__device__ __forceinline__ void vq25(const At &at, Pf p25f, V &sx, V &sy)
-{
-    V ax = vsplat(0.f, V{}), ay = vsplat(0.f, V{});
-#pragma unroll
-    for (int a = 1; a <= 2; ++a) {
-        const float p = p25f(a * a) * (float)a;
-        ax = cfma(p, vsub(at(0, a), at(0, -a)), ax);
-        ay = cfma(p, vsub(at(a, 0), at(-a, 0)), ay);
-    }
-#pragma unroll
-    for (int a = 1; a <= 2; ++a)
-#pragma unroll
-        for (int b = 1; b <= 2; ++b) {
-            const V d1 = vsub(at(b, a), at(-b, -a));   // (a,b) - (-a,-b)
-            const V d2 = vsub(at(-b, a), at(b, -a));   // (a,-b) - (-a,b)
-            const float p = p25f(a * a + b * b);
-            ax = cfma(p * (float)a, vadd(d1, d2), ax);
-            ay = cfma(p * (float)b, vsub(d1, d2), ay);
-        }
-    sx = ax;
-    sy = ay;
-}
-
 // -sum_j c_j s(x + e_j) e_j over D2Q25 with the weights of the two psi sums
 // of Eq. (8) combined, c(|e|^2) = G1 w(|e|^2) + G2 p(|e|^2): the near
 // cancellation of the attraction and the repulsion on the inner ring
