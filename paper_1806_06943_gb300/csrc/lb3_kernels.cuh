@@ -26,6 +26,7 @@
 
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stddef.h>
 #include <stdint.h>
 
 namespace lbk3 {
@@ -83,6 +84,9 @@ __device__ __forceinline__ int wrap3(int a, int n)
     return a < 0 ? a + n : a;
 }
 
+// a periodic index one period off at most (a in [-n, 2n)): no division
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
 __device__ __forceinline__ void tile_origin(int tiles_x, int tiles_y, int b, int &x0, int &y0, int &z0)
 {
     x0 = (b % tiles_x) * TX;
@@ -108,9 +112,14 @@ template <typename real>
 __device__ __forceinline__ void stage3(const Lat3<real> &L, const real *__restrict__ rho, int x0, int y0, int z0,
                                        Stage3<real> &sm, int tid)
 {
+    // the slots' coordinates lie within one period of the lattice when each
+    // side is at least a tile plus both halos (a block-uniform choice)
+    const bool near = L.nx >= SX && L.ny >= SY && L.nz >= SZ;
     for (int idx = tid; idx < SX * SY * SZ; idx += kThreads) {
         const int sx = idx % SX, sy = (idx / SX) % SY, sz = idx / (SX * SY);
-        const int gx = wrap3(x0 + sx - HALO, L.nx), gy = wrap3(y0 + sy - HALO, L.ny), gz = wrap3(z0 + sz - HALO, L.nz);
+        const int ax = x0 + sx - HALO, ay = y0 + sy - HALO, az = z0 + sz - HALO;
+        const int gx = near ? wrap1(ax, L.nx) : wrap3(ax, L.nx), gy = near ? wrap1(ay, L.ny) : wrap3(ay, L.ny);
+        const int gz = near ? wrap1(az, L.nz) : wrap3(az, L.nz);
         const size_t c = ((size_t)gz * L.ny + gy) * L.pitch + gx;
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
@@ -212,8 +221,10 @@ __global__ void __launch_bounds__(kThreads) k3_density(const Lat3<real> L, int p
 // 48 KB of static shared memory): the stage, then the observation partials.
 extern __shared__ __align__(16) unsigned char lb3_smem[];
 
+// FP32: three blocks per SM (80 registers; the spill of a few values costs
+// less than the latency a third block hides), FP64: as many as fit.
 template <typename real>
-__global__ void __launch_bounds__(kThreads) k3_collide(const Lat3<real> L, int parity)
+__global__ void __launch_bounds__(kThreads, kOffset3<real> ? 3 : 1) k3_collide(const Lat3<real> L, int parity)
 {
     Stage3<real> &sm = *reinterpret_cast<Stage3<real> *>(lb3_smem);
     int x0, y0, z0;
@@ -300,7 +311,7 @@ __global__ void __launch_bounds__(kThreads) k3_collide(const Lat3<real> L, int p
                 // re-referenced to the destination's density (its next R)
                 if (i != 0) v += w * (rho[k] - sm.rho[k][cz + EZ][cy + EY][cx + EX]);
             }
-            const int xd = wrap3(x + EX, L.nx), yd = wrap3(y + EY, L.ny), zd = wrap3(z + EZ, L.nz);
+            const int xd = wrap1(x + EX, L.nx), yd = wrap1(y + EY, L.ny), zd = wrap1(z + EZ, L.nz);
             fn[(size_t)(k * 19 + i) * L.plane + ((size_t)zd * L.ny + yd) * L.pitch + xd] = v;
         }
     }
