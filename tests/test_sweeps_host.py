@@ -88,3 +88,18 @@ def test_disjoining_pressure_quadrature_against_a_closed_form(oracle_mod):
         assert np.max(np.abs(Pi - exact)) <= 3e-5 * np.max(np.abs(exact))   # trapezoid, dh = 0.0095
     assert np.allclose(oracle_mod.disjoining_pressure(h[::20], s[::20]),
                        sweeps.disjoining_pressure(h[::20], s[::20]), rtol=0, atol=1e-15)
+
+
+def test_droplet_array_noise_option():
+    """The rheology arrays start exactly symmetric with noise=0: two density
+    values only, and the 25 cells of the 5 x 5 array (44 x 44 nodes each)
+    are identical."""
+    from paper_1806_06943_gb300 import sweeps as S
+    from paper_1806_06943_gb300 import workloads as W
+    rho, phi = S.droplet_array(220, 5, 16.5, seed=W.BASE_SEED + 12, noise=0.0)
+    assert set(np.unique(rho[0]).tolist()) == {W.MINORITY, W.MAJORITY}
+    cells = [rho[:, 44 * j:44 * j + 44, 44 * i:44 * i + 44] for j in range(5) for i in range(5)]
+    assert all(np.array_equal(c, cells[0]) for c in cells)
+    assert abs(phi - 0.445) < 0.005
+    noisy, _ = S.droplet_array(220, 5, 16.5, seed=W.BASE_SEED + 12)
+    assert 0 < np.max(np.abs(noisy - rho)) <= W.NOISE * (1 + 1e-12)
