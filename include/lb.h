@@ -302,6 +302,17 @@ int lb_profile(lb_handle *h, int32_t nsteps, void *flush_buf, size_t flush_bytes
  * population copies, plus 22 FP64 planes.  Synchronises. */
 int lb_grad(lb_handle *h, int64_t nsteps, int32_t ckpt_every, int32_t objective, double *J, double dJ[5]);
 
+/* One step of the discrete adjoint at the current state (the transpose of
+ * the linearised time step, Eqs. 1-3, 5, 6, 8, 9 with streaming and
+ * bounce-back): for host w[2][9][ny][nx] (population order of
+ * lb_get_populations), out = (dStep/df)^T w and dtheta = <w, dStep/dtheta>
+ * for theta = (G_AB, G1, G2, tau_A, tau_B), Step the map from the
+ * populations at time t to those at t + 1.  Either output may be NULL.
+ * LB_FP64 lattices with Guo forcing only (else LB_EINVAL).  The state is
+ * not changed.  Device memory: two FP64 population copies and 22 FP64
+ * planes, allocated for the call.  Synchronises. */
+int lb_step_vjp(lb_handle *h, const double *w, double *out, double dtheta[5]);
+
 /* ---- many independent lattices advanced together ------------------------- */
 
 /* Create n >= 1 lattices of possibly different sizes and parameters that

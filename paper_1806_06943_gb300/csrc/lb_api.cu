@@ -806,6 +806,59 @@ struct lb_engine {
         return done(end());
     }
 
+    // One adjoint step at the current state (FP64): out = (dStep/df)^T w and
+    // dtheta = <w, dStep/dtheta>, theta = (G_AB, G1, G2, tau_A, tau_B); host
+    // arrays [2][9][ny][nx]; the state is left as it was.
+    int step_vjp(const double *w, double *out, double dtheta[5])
+    {
+        if (precision != LB_FP64) return fail(LB_EINVAL, "lb_step_vjp needs LB_FP64 populations");
+        if (P[0].forcing != LB_FORCING_GUO) return fail(LB_EINVAL, "lb_step_vjp is the adjoint of the Guo-forcing step only");
+        if (!w) return fail(LB_EINVAL, "w is NULL");
+        int rc = begin();
+        if (rc) return rc;
+        const lb_params &p = P[0];
+        const lbk::Lat<double> &L = L64[0];
+        const size_t plane_b = plane(0) * sizeof(double), pop64 = 18 * plane_b;
+        const int ntl = ((p.nx + lbk::TX - 1) / lbk::TX) * ((p.ny + lbk::TY - 1) / lbk::TY);
+        const size_t bytes = 2 * pop64 + lbk::kAdjSlotCount * plane_b + 2 * plane_b + (size_t)ntl * 8 * sizeof(double) +
+                             8 * sizeof(double);
+        char *mem = nullptr;
+        if (cudaMalloc((void **)&mem, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LB_ENOMEM, "lb_step_vjp: no room for the adjoint buffers");
+        }
+        char *q = mem;
+        auto take = [&](size_t b) { char *r = q; q += b; return r; };
+        double *lam_in = (double *)take(pop64), *lam_out = (double *)take(pop64);
+        double *abuf = (double *)take(lbk::kAdjSlotCount * plane_b), *rho = (double *)take(2 * plane_b);
+        double *gpart = (double *)take((size_t)ntl * 8 * sizeof(double)), *gout = (double *)take(8 * sizeof(double));
+        const double *f = (const double *)fbuf(0, parity);
+        const size_t row = (size_t)p.nx * sizeof(double), prow = (size_t)L.pitch * sizeof(double);
+        cudaError_t ce = cudaMemsetAsync(mem, 0, 2 * pop64, stream);   // the pitch padding stays zero
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(gpart, 0, (size_t)ntl * 8 * sizeof(double), stream);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy2DAsync(lam_in, prow, w, row, row, (size_t)18 * p.ny, cudaMemcpyHostToDevice, stream);
+        if (ce == cudaSuccess) ce = lbk::adj_density(L, f, rho, stream);
+        if (ce == cudaSuccess) ce = lbk::adj_step(L, f, rho, lam_in, abuf, gpart, lam_out, 0, 0.0, 0.0, stream);
+        if (ce == cudaSuccess) ce = lbk::adj_reduce(gpart, ntl, gout, stream);
+        double g[8] = {0};
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(g, gout, 8 * sizeof(double), cudaMemcpyDeviceToHost, stream);
+        if (ce == cudaSuccess && out)
+            ce = cudaMemcpy2DAsync(out, row, lam_out, prow, row, (size_t)18 * p.ny, cudaMemcpyDeviceToHost, stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+        cudaStreamSynchronize(stream);
+        cudaFree(mem);
+        if (ce != cudaSuccess) return cuda_fail(ce, "lb_step_vjp");
+        if (dtheta) {   // d omega / d tau = -omega^2
+            dtheta[0] = g[0];
+            dtheta[1] = g[1];
+            dtheta[2] = g[2];
+            dtheta[3] = -g[3] * L.omega[0] * L.omega[0];
+            dtheta[4] = -g[4] * L.omega[1] * L.omega[1];
+        }
+        return end();
+    }
+
     int observables(lb_obs *o)
     {
         int rc = begin();
@@ -1252,6 +1305,12 @@ int lb_pressure_tensor(lb_handle *h, double *P, double sums[6])
 {
     CHECK_H(h);
     return h->e->pressure(0, P, sums);
+}
+
+int lb_step_vjp(lb_handle *h, const double *w, double *out, double dtheta[5])
+{
+    CHECK_H(h);
+    return h->e->step_vjp(w, out, dtheta);
 }
 
 int lb_get_populations(lb_handle *h, double *f)

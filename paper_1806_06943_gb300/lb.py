@@ -116,6 +116,7 @@ SIGNATURES = {
     "lb_observables": (ctypes.c_int, [_vp, _P(lb_obs)]),
     "lb_get_fields": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lb_get_populations": (ctypes.c_int, [_vp, _vp]),
+    "lb_step_vjp": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lb_set_populations": (ctypes.c_int, [_vp, _vp, _i64]),
     "lb_save": (ctypes.c_int, [_vp, _vp, _P(_sz)]),
     "lb_load": (ctypes.c_int, [_vp, _vp, _sz]),
@@ -297,6 +298,15 @@ class Lattice:
         P = np.empty((2, 3, self.ny, self.nx)) if field else None
         _check(LIB.lb_pressure_tensor(self.h, P.ctypes.data if field else None, sums.ctypes.data))
         return sums, P
+
+    def step_vjp(self, w: np.ndarray) -> tuple:
+        """((dStep/df)^T w, <w, dStep/dtheta>) at the current state (FP64)."""
+        ny, nx = self.ny, self.nx
+        wa = np.ascontiguousarray(w, dtype=np.float64)   # kept alive across the call
+        out = np.empty((2, 9, ny, nx))
+        dth = (ctypes.c_double * 5)()
+        _check(LIB.lb_step_vjp(self.h, _host_ptr(wa, (2, 9, ny, nx)), out.ctypes.data, dth))
+        return out, np.array(list(dth))
 
     def get_populations(self) -> np.ndarray:
         f = np.empty((2, 9, self.ny, self.nx))

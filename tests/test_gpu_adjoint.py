@@ -12,7 +12,12 @@ populations for the FP64 adjoint) is held to the same 1e-4 against the FP64
 gradient and the FP64 finite differences: it differs from them by 2e-5 to
 4e-5.  Finite differences of the FP32 forward itself are no reference: its
 mu_r carries rounding of ~1e-6 relative, which h = 1e-4 turns into errors of
-~1e-2."""
+~1e-2.
+
+One adjoint step on its own (lb_step_vjp): <J v, w> = <v, J^T w> for the
+linearised time step J, with J v from central differences of the FP64
+forward step, and <w, dStep/dtheta> against central differences in each
+parameter."""
 import numpy as np
 import pytest
 
@@ -175,3 +180,58 @@ def test_rejects_unsupported(lbmod):
         P.grad(10, 5, lbmod.LB_OBJ_MU_R)
     with pytest.raises(lbmod.LBError):   # no probe
         P.grad(10, 5, lbmod.LB_OBJ_DP)
+
+
+@pytest.mark.parametrize("walls", [0, 1])
+def test_step_vjp_dot_product(lbmod, walls):
+    """The transpose of one linearised time step against the step itself:
+    <J v, w> = <v, J^T w> for random v, w (J v by central differences of
+    the FP64 forward step, eps = 1e-6), to 1e-7 relative; and the parameter
+    part <w, dStep/dtheta> against central differences in G_AB, G1, G2,
+    tau_A, tau_B, to 1e-6 relative.  A 20 x 16 drop after 20 steps,
+    periodic, and with non-wetting walls and a body force."""
+    nx, ny = 20, 16
+    kw = dict(tau=(0.9, 1.3), G_AB=3.0, G1=-7.4, G2=6.4)
+    if walls:
+        kw.update(walls=1, wall_mode=1, wall_rho=(0.03, 1.0), g=(1e-5, 0.0))
+    rho = W.droplet(nx, ny, 5.0, seed=7, periodic=not walls)
+    L = lbmod.Lattice(nx, ny, **kw)
+    L.set_fields(rho)
+    L.step(20)
+    f0 = L.get_populations()
+    rng = np.random.default_rng(3 + walls)
+    v = rng.standard_normal(f0.shape) * np.max(np.abs(f0))
+    w = rng.standard_normal(f0.shape)
+
+    def step_from(f, **over):
+        K = lbmod.Lattice(nx, ny, **{**kw, **over})
+        K.set_populations(np.ascontiguousarray(f))
+        K.step(1)
+        return K.get_populations()
+
+    eps = 1e-6
+    Jv = (step_from(f0 + eps * v) - step_from(f0 - eps * v)) / (2 * eps)
+    JTw, dth = L.step_vjp(w)
+    assert np.array_equal(L.get_populations(), f0)   # the state is left as it was
+    lhs, rhs = float(np.sum(Jv * w)), float(np.sum(v * JTw))
+    assert abs(lhs - rhs) <= 1e-7 * abs(rhs), (lhs, rhs)
+    for i, name in enumerate(("G_AB", "G1", "G2")):
+        h = 1e-5 * abs(kw[name])
+        d = (step_from(f0, **{name: kw[name] + h}) - step_from(f0, **{name: kw[name] - h})) / (2 * h)
+        ref = float(np.sum(w * d))
+        assert abs(ref - dth[i]) <= 1e-6 * abs(ref), (name, ref, dth[i])
+    for k in (0, 1):
+        h = 1e-5
+        tp, tm = list(kw["tau"]), list(kw["tau"])
+        tp[k] += h
+        tm[k] -= h
+        d = (step_from(f0, tau=tuple(tp)) - step_from(f0, tau=tuple(tm))) / (2 * h)
+        ref = float(np.sum(w * d))
+        assert abs(ref - dth[3 + k]) <= 1e-6 * abs(ref), (k, ref, dth[3 + k])
+
+
+def test_step_vjp_rejects_fp32(lbmod):
+    L = lbmod.Lattice(20, 16, precision=lbmod.LB_FP32)
+    with pytest.raises(lbmod.LBError) as ei:
+        L.step_vjp(np.zeros((2, 9, 16, 20)))
+    assert ei.value.code == lbmod.LB_EINVAL
