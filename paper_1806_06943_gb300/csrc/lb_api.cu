@@ -46,6 +46,7 @@ int cuda_fail(cudaError_t e, const char *what)
 
 constexpr int kGraphSteps = 32;   // steps per captured graph (even: parity returns)
 constexpr int kPersistSteps = 64; // time steps per persistent launch
+constexpr int kChains = 2;         // chains of time steps of a batch's step graph
 constexpr int kTileHeights[3] = {2, 4, 8};
 
 int ty_index(int ty) { return ty == 2 ? 0 : (ty == 4 ? 1 : (ty == 8 ? 2 : -1)); }
@@ -185,6 +186,18 @@ struct lb_engine {
     int64_t t = 0;
     int parity = 0;
     cudaGraphExec_t gexec = nullptr;
+    // Chains of time steps for a batch: the lattices split into kChains
+    // groups of about equal node counts, each group's steps launched on its
+    // own stream (the engine's for group 0, an auxiliary one for each other)
+    // and captured as independent branches of the step graph, so that the
+    // launches of one group fill the last waves of the others'.  Per tile
+    // height, the tiles of group 0 (the TMA box tiles first, then the rest),
+    // then those of group 1, and so on.
+    int nchains = 1;
+    cudaStream_t aux[kChains] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kChains] = {};
+    int4 *d_ctiles[3] = {nullptr, nullptr, nullptr};
+    int c_off[3][kChains] = {}, c_box[3][kChains] = {}, c_cnt[3][kChains] = {};
 
     ~lb_engine()
     {
@@ -205,6 +218,15 @@ struct lb_engine {
         cudaFree(d_obs);
         cudaFree(d_psum);
         cudaFree(d_tmp);
+        for (int i = 0; i < 3; ++i) cudaFree(d_ctiles[i]);
+        for (int g = 0; g < kChains; ++g) {
+            if (aux[g]) {
+                cudaStreamSynchronize(aux[g]);
+                cudaStreamDestroy(aux[g]);
+            }
+            if (ev_join[g]) cudaEventDestroy(ev_join[g]);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
         if (stream && own_stream) cudaStreamDestroy(stream);
     }
 
@@ -289,13 +311,57 @@ struct lb_engine {
                                               nsteps, par, d_ctl, dens, coll, d_err, wait_cycles, drop_tile, ty,
                                               blocks, stream);
     }
-    // time steps in the current mode, as captured into one graph
+    // one time step of the lattices of chain g on stream s
+    cudaError_t launch_chain_step(int g, int par, cudaStream_t s)
+    {
+        const int ti = ty_index(ty), off = c_off[ti][g], nb = c_box[ti][g], cnt = c_cnt[ti][g];
+        const int4 *T = d_ctiles[ti];
+        if (cnt == 0) return cudaSuccess;
+        cudaError_t e;
+        if (precision == LB_FP64) {
+            const lbk::Lat<double> *L = (const lbk::Lat<double> *)d_lats;
+            if (mode == LB_MODE_FUSED) return lbk::Launch<double>::fused(L, T, off, cnt, par, ty, s);
+            e = lbk::Launch<double>::density(L, T, off, cnt, par, ty, s);
+            if (e == cudaSuccess) e = lbk::Launch<double>::collide(L, T, off, cnt, par, ty, s);
+            return e;
+        }
+        const lbk::Lat<float> *L = (const lbk::Lat<float> *)d_lats;
+        if (mode == LB_MODE_FUSED) return lbk::Launch<float>::fused(L, T, off, cnt, par, ty, s);
+        if (mode == LB_MODE_TMA) {
+            e = lbk::launch_fused_tma(L, T, off, nb, par, d_tmaps, d_err, wait_cycles, drop_tile, ty, s);
+            if (e == cudaSuccess && cnt > nb) e = lbk::Launch<float>::fused(L, T, off + nb, cnt - nb, par, ty, s);
+            return e;
+        }
+        e = lbk::Launch<float>::density(L, T, off, cnt, par, ty, s);
+        if (e == cudaSuccess) e = lbk::Launch<float>::collide(L, T, off, cnt, par, ty, s);
+        return e;
+    }
+    // time steps in the current mode, as captured into one graph: with
+    // chains, chains 1.. fork onto their auxiliary streams and join the
+    // engine's stream again at the end (also after a failed launch, so that
+    // a capture always ends joined)
     cudaError_t launch_chunk(int par, int nsteps)
     {
         if (mode == LB_MODE_PERSISTENT) return launch_persistent(par, nsteps);
         cudaError_t e = cudaSuccess;
-        for (int s = 0; s < nsteps && e == cudaSuccess; ++s) e = launch_step((par + s) & 1);
-        return e;
+        if (nchains < 2) {
+            for (int s = 0; s < nsteps && e == cudaSuccess; ++s) e = launch_step((par + s) & 1);
+            return e;
+        }
+        e = cudaEventRecord(ev_fork, stream);
+        int forked = 1;
+        for (; forked < nchains && e == cudaSuccess; ++forked) e = cudaStreamWaitEvent(aux[forked], ev_fork, 0);
+        if (e != cudaSuccess) --forked;
+        for (int s = 0; s < nsteps && e == cudaSuccess; ++s)
+            for (int g = 0; g < nchains && e == cudaSuccess; ++g)
+                e = launch_chain_step(g, (par + s) & 1, g ? aux[g] : stream);
+        cudaError_t j = cudaSuccess;
+        for (int g = 1; g < forked; ++g) {
+            cudaError_t r = cudaEventRecord(ev_join[g], aux[g]);
+            if (r == cudaSuccess) r = cudaStreamWaitEvent(stream, ev_join[g], 0);
+            if (j == cudaSuccess) j = r;
+        }
+        return e != cudaSuccess ? e : j;
     }
     int chunk_steps() const { return mode == LB_MODE_PERSISTENT ? kPersistSteps : kGraphSteps; }
     void drop_graph()
@@ -1174,6 +1240,54 @@ int engine_create(const lb_params *p, int n, lb_engine **out)
     if (e->precision == LB_FP32) {
         const int rc = e->build_tma_maps();
         if (rc) return bail(rc);
+    }
+    // the chains of a batch's step graph (as many as lattices, at most
+    // kChains): lattices by node count, each to the group with the fewest
+    // nodes so far
+    if (n >= 2) {
+        const int nc = std::min(n, kChains);
+        std::vector<int> order(n), group(n, 0);
+        for (int l = 0; l < n; ++l) order[l] = l;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return (int64_t)p[a].nx * p[a].ny > (int64_t)p[b].nx * p[b].ny;
+        });
+        int64_t load[kChains] = {};
+        for (int l : order) {
+            int g = 0;
+            for (int k = 1; k < nc; ++k)
+                if (load[k] < load[g]) g = k;
+            group[l] = g;
+            load[g] += (int64_t)p[l].nx * p[l].ny;
+        }
+        for (int ti = 0; ti < 3; ++ti) {
+            const int tyv = kTileHeights[ti];
+            std::vector<int4> list;
+            for (int g = 0; g < nc; ++g) {
+                e->c_off[ti][g] = (int)list.size();
+                for (int pass = 0; pass < 2; ++pass) {
+                    for (const int4 &t : e->stiles[ti])
+                        if (group[t.x] == g && lbk::tma_box_tile(p[t.x].nx, p[t.x].ny, t.y, t.z, tyv) == (pass == 0))
+                            list.push_back(t);
+                    if (pass == 0) e->c_box[ti][g] = (int)list.size() - e->c_off[ti][g];
+                }
+                e->c_cnt[ti][g] = (int)list.size() - e->c_off[ti][g];
+            }
+            if (cudaMalloc((void **)&e->d_ctiles[ti], list.size() * sizeof(int4)) != cudaSuccess) {
+                cudaGetLastError();
+                return bail(fail(LB_ENOMEM, "cudaMalloc of the chain tile lists failed"));
+            }
+            if ((ce = cudaMemcpyAsync(e->d_ctiles[ti], list.data(), list.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                      e->stream)) != cudaSuccess ||
+                (ce = cudaStreamSynchronize(e->stream)) != cudaSuccess)
+                return bail(cuda_fail(ce, "chain tile list upload"));
+        }
+        if ((ce = cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming)) != cudaSuccess)
+            return bail(cuda_fail(ce, "cudaEventCreateWithFlags"));
+        for (int g = 1; g < nc; ++g)
+            if ((ce = cudaStreamCreateWithFlags(&e->aux[g], cudaStreamNonBlocking)) != cudaSuccess ||
+                (ce = cudaEventCreateWithFlags(&e->ev_join[g], cudaEventDisableTiming)) != cudaSuccess)
+                return bail(cuda_fail(ce, "auxiliary streams of the step graph"));
+        e->nchains = nc;
     }
     *out = e;
     return LB_OK;
