@@ -220,16 +220,26 @@ struct SplitStage {
     {
         force_at<real, SHv>(L, srho, spsi, k, cx, cy, Fx, Fy);
     }
+    // FP32: both species' forces and densities as (A, B) pairs
+    __device__ __forceinline__ void force2(const Lat<float> &L, int cx, int cy, float2 &Fx, float2 &Fy) const
+    {
+        force_at<float, SHv>(L, srho, spsi, 0, cx, cy, Fx.x, Fy.x);
+        force_at<float, SHv>(L, srho, spsi, 1, cx, cy, Fx.y, Fy.y);
+    }
+    __device__ __forceinline__ float2 density2(int cy, int cx) const
+    {
+        return make_float2(srho[0][cy][cx], srho[1][cy][cx]);
+    }
     template <int EX, int EY>
     __device__ __forceinline__ real density_step(int k, int cx, int cy) const
     {
         return srho[k][cy][cx] - srho[k][cy + EY][cx + EX];
     }
-    // both species' densities at the staged node (cx + EX, cy + EY)
+    // FP32: both species' densities at the staged node (cx + EX, cy + EY)
     template <int EX, int EY>
-    __device__ __forceinline__ Sp<real> dest(int cx, int cy) const
+    __device__ __forceinline__ float2 dest(int cx, int cy) const
     {
-        return {srho[0][cy + EY][cx + EX], srho[1][cy + EY][cx + EX]};
+        return make_float2(srho[0][cy + EY][cx + EX], srho[1][cy + EY][cx + EX]);
     }
 };
 
@@ -269,13 +279,14 @@ __device__ __forceinline__ real collide_dir(real f, real rho, real ux, real uy, 
 
 // Store the post-collision value of direction I of species k at x + e_i
 // (half-way bounce-back: back to x, reversed).  FP32: re-reference the offset
-// from rho(x) to rho(x + e_i), the reference the next step reads there.
-template <typename real, int I, bool kInner, class Stage>
+// from rho(x) to rho(x + e_i), the reference the next step reads there
+// (unless kReref is false: the caller did).
+template <typename real, int I, bool kInner, class Stage, bool kReref = true>
 __device__ __forceinline__ void push_dir(const Lat<real> &L, real *__restrict__ fn, const Stage &sg, int k, int x,
                                          int y, int cx, int cy, real v)
 {
     constexpr int EX = ex9(I), EY = ey9(I);
-    if constexpr (kOffset<real> && I != 0) {
+    if constexpr (kOffset<real> && kReref && I != 0) {
         // the next step's reference at the destination is its density now
         if (kInner || !(EY != 0 && L.walls && (y + EY < 0 || y + EY >= L.ny)))
             v = cfma((float)w9(I), sg.template density_step<EX, EY>(k, cx, cy), v);
@@ -391,21 +402,21 @@ struct CollideSmem {
     Lat<real> L;   // descriptor copy: stores to the populations cannot alias it
 };
 
-// Moments of a node's FP32 offset populations that need no force: the first
-// moment per species, the density change rho - R moved into the offsets and
-// the offsets' residual sum dg after it (collide_site explains both).
-template <typename real>
+// Moments of a node's FP32 offset populations that need no force, as
+// (species A, species B) pairs: the first moment, the density change rho - R
+// moved into the offsets and the offsets' residual sum dg after it
+// (collide_site explains both).
 struct NodeMoments {
-    real j[2][2];
-    real delta[2];
-    real dg[2];
+    float2 jx, jy;
+    float2 delta;
+    float2 dg;
 };
 
 template <typename real, bool kInner, bool kBox = false, class Stage>
 __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const Stage &sg,
                                              real (&fk)[2][9], const real (&Rn)[2], int x, int y, int cx, int cy,
                                              const real *__restrict__ box = nullptr, int box_plane = 0,
-                                             const NodeMoments<real> *pre = nullptr);
+                                             const NodeMoments *pre = nullptr);
 
 // Fused force + collision + push-streaming + bounce-back for one tile.  Every
 // thread of the block calls it and returns from it; it ends after the tile's
@@ -492,24 +503,19 @@ __global__ void __launch_bounds__(TX *TYv, kCollideMinBlocks<real, TYv>)
 }
 
 // The NodeMoments of a node whose populations are in a shared-memory box
-// (box[(k * 9 + i) * box_plane]), rho its density and Rn its reference: the
-// same operations, in the same order, as collide_site's own loop.
-template <typename real>
-__device__ __forceinline__ void node_moments(const real *__restrict__ box, int box_plane, const real (&rho)[2],
-                                             const real (&Rn)[2], NodeMoments<real> &nm)
+// (box[(k * 9 + i) * box_plane]), rho its densities and Rn its references:
+// the same operations, in the same order, as collide_site's own.
+__device__ __forceinline__ void node_moments(const float *__restrict__ box, int box_plane, float2 rho, float2 Rn,
+                                             NodeMoments &nm)
 {
-    static_assert(kOffset<real>, "the box form is FP32 only");
+    float2 f[9];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        float f[9];
+    for (int i = 0; i < 9; ++i) f[i] = make_float2(box[i * box_plane], box[(9 + i) * box_plane]);
+    vfirst<float2>(f, nm.jx, nm.jy);
+    nm.delta = vsub(rho, Rn);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = box[(k * 9 + i) * box_plane];
-        vfirst<float>(f, nm.j[k][0], nm.j[k][1]);
-        nm.delta[k] = vsub(rho[k], Rn[k]);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = cfma(-(float)w9(i), nm.delta[k], f[i]);
-        nm.dg[k] = vzeroth<float>(f);
-    }
+    for (int i = 0; i < 9; ++i) f[i] = cfma(-(float)w9(i), nm.delta, f[i]);
+    nm.dg = vzeroth<float2>(f);
 }
 
 // ---- velocity-shift forcing of the original model (FP64 only) ---------------
@@ -588,69 +594,69 @@ __device__ __forceinline__ void shift_collide_site(const Lat<real> &L, real *__r
 template <bool kInner, bool kBox, class Stage>
 __device__ __forceinline__ void collide_site_off(const Lat<float> &L, float *__restrict__ fn, const Stage &sg,
                                                  float (&fk)[2][9], const float (&Rn)[2], int x, int y, int cx, int cy,
-                                                 const float *__restrict__ box, int box_plane,
-                                                 const NodeMoments<float> *pre)
+                                                 const float *__restrict__ box, int box_plane, const NodeMoments *pre)
 {
-    float F[2][2], rho[2], m[2][2], dg[2], delta[2];
+    // both species at once, as (A, B) pairs
+    float2 Fx, Fy, jx, jy, delta, dg;
+    sg.force2(L, cx, cy, Fx, Fy);
+    const float2 rho = sg.density2(cy, cx);
+    float2 h[9];
+    if constexpr (kBox) {
+        (void)fk;
+        (void)Rn;
+        jx = pre->jx;
+        jy = pre->jy;
+        delta = pre->delta;
+        dg = pre->dg;
+    } else {
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        sg.force(L, k, cx, cy, F[k][0], F[k][1]);
-        rho[k] = sg.density(k, cy, cx);
-        float jx, jy;
-        if constexpr (kBox) {
-            jx = pre->j[k][0];
-            jy = pre->j[k][1];
-            delta[k] = pre->delta[k];
-            dg[k] = pre->dg[k];
-        } else {
-            float(&f)[9] = fk[k];
-            vfirst<float>(f, jx, jy);   // the reference density adds no momentum
-            // offsets from the node's current density: h_i - w_i (rho - R).
-            // rho - R is formed from the rounded density itself (exact: the two
-            // are close), so f = h + w R is kept exactly whatever rho rounded to;
-            // with sum_i h_i instead, density changes below half an ulp of R
-            // would be dropped at every step and mass would drift.
-            delta[k] = vsub(rho[k], Rn[k]);
+        for (int i = 0; i < 9; ++i) h[i] = make_float2(fk[0][i], fk[1][i]);
+        vfirst<float2>(h, jx, jy);   // the reference density adds no momentum
+        // offsets from the node's current density: h_i - w_i (rho - R).
+        // rho - R is formed from the rounded density itself (exact: the two
+        // are close), so f = h + w R is kept exactly whatever rho rounded to;
+        // with sum_i h_i instead, density changes below half an ulp of R
+        // would be dropped at every step and mass would drift.
+        delta = vsub(rho, make_float2(Rn[0], Rn[1]));
 #pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = cfma(-(float)w9(i), delta[k], f[i]);
-            dg[k] = vzeroth<float>(f);
-        }
-        m[k][0] = cfma(0.5f, F[k][0], jx);   // Eq. (6), half force
-        m[k][1] = cfma(0.5f, F[k][1], jy);
+        for (int i = 0; i < 9; ++i) h[i] = cfma(-(float)w9(i), delta, h[i]);
+        dg = vzeroth<float2>(h);
     }
-    OffTerms<float> t;
-    off_terms<float>(L.omega[0], L.omega[1], rho, m, F, dg, t);
+    const float2 mx = cfma(0.5f, Fx, jx);   // Eq. (6), half force
+    const float2 my = cfma(0.5f, Fy, jy);
     // the lattice constants of the collision, read once: stores to the
     // populations may alias shared memory as far as the compiler knows
-    const float om[2] = {L.omega[0], L.omega[1]};
-    const float aw3[2][3] = {{L.aw3[0][0], L.aw3[0][1], L.aw3[0][2]}, {L.aw3[1][0], L.aw3[1][1], L.aw3[1][2]}};
+    const float2 om = make_float2(L.omega[0], L.omega[1]);
+    const float2 aw3[3] = {make_float2(L.aw3[0][0], L.aw3[1][0]), make_float2(L.aw3[0][1], L.aw3[1][1]),
+                           make_float2(L.aw3[0][2], L.aw3[1][2])};
+    OffTerms t;
+    off_terms(om, rho, mx, my, Fx, Fy, dg, t);
     const size_t plane = L.plane;
     const int pitch = L.pitch;
     float *node = fn + ((size_t)y * pitch + x);
-    // the population of direction I of species k, as the moments saw it
-    auto pop = [&](int k, int I) -> float {
-        if constexpr (kBox) return cfma(-(float)w9(I), delta[k], box[(k * 9 + I) * box_plane]);
-        else return fk[k][I];
+    // the populations of direction I, as the moments saw them
+    auto pop = [&](int I) -> float2 {
+        if constexpr (kBox)
+            return cfma(-(float)w9(I), delta, make_float2(box[I * box_plane], box[(9 + I) * box_plane]));
+        else return h[I];
     };
-    Sp<float> dest{0.f, 0.f};
     auto dir = [&](auto Ic) {
         constexpr int I = decltype(Ic)::value;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            float v = off_collide<I, float>(t, k, om[k], aw3[k][cls9(I)], pop(k, I));
-            if constexpr (kInner) {
-                // destination inside the lattice: re-reference from rho(x) to
-                // rho(x + e_i), the reference the next step reads there, and
-                // store at a constant offset
-                constexpr int EX = ex9(I), EY = ey9(I);
-                if constexpr (I != 0) {
-                    if (k == 0) dest = sg.template dest<EX, EY>(cx, cy);
-                    v = cfma((float)w9(I), vsub(rho[k], k ? dest.b : dest.a), v);
-                }
-                node[(size_t)(k * 9 + I) * plane + (EY * pitch + EX)] = v;
-            } else {
-                push_dir<float, I, kInner>(L, fn, sg, k, x, y, cx, cy, v);
-            }
+        float2 v = off_collide<I>(t, om, aw3[cls9(I)], pop(I));
+        // re-reference from rho(x) to rho(x + e_i), the reference the next
+        // step reads there (not for a push that bounces back from a wall)
+        constexpr int EX = ex9(I), EY = ey9(I);
+        if constexpr (I != 0) {
+            if (kInner || !(EY != 0 && L.walls && (y + EY < 0 || y + EY >= L.ny)))
+                v = cfma((float)w9(I), vsub(rho, sg.template dest<EX, EY>(cx, cy)), v);
+        }
+        if constexpr (kInner) {
+            // destination inside the lattice: a constant offset
+            node[(size_t)I * plane + (EY * pitch + EX)] = v.x;
+            node[(size_t)(9 + I) * plane + (EY * pitch + EX)] = v.y;
+        } else {
+            push_dir<float, I, kInner, Stage, false>(L, fn, sg, 0, x, y, cx, cy, v.x);
+            push_dir<float, I, kInner, Stage, false>(L, fn, sg, 1, x, y, cx, cy, v.y);
         }
     };
     dir(std::integral_constant<int, 0>{});
@@ -673,7 +679,7 @@ __device__ __forceinline__ void collide_site_off(const Lat<float> &L, float *__r
 template <typename real, bool kInner, bool kBox, class Stage>
 __device__ __forceinline__ void collide_site(const Lat<real> &L, real *__restrict__ fn, const Stage &sg,
                                              real (&fk)[2][9], const real (&Rn)[2], int x, int y, int cx, int cy,
-                                             const real *__restrict__ box, int box_plane, const NodeMoments<real> *pre)
+                                             const real *__restrict__ box, int box_plane, const NodeMoments *pre)
 {
     static_assert(!kBox || kOffset<real>, "the box form is FP32 only");
     if constexpr (kOffset<real>) {

@@ -106,54 +106,28 @@ struct PairSmem {
 };
 
 // The pair planes as collide_site reads them (the interface of SplitStage):
-// species 0's force and density step are formed together with species 1's,
-// which are kept for the call that follows for species 1.
+// both species' forces of Eqs. (8), (9) and rho_k g, their densities, and
+// the densities a push re-references with, each as an (A, B) pair.
 template <int SHv>
 struct PairStage {
     const float2 (*sr)[SW];
     const float2 (*sp)[SW];
-    mutable float F1x, F1y, d1;
-    __device__ __forceinline__ float density(int k, int cy, int cx) const
+    __device__ __forceinline__ float2 density2(int cy, int cx) const { return sr[cy][cx]; }
+    // Eq. (8) + Eq. (9) + rho_k g, the operations of force_at on each lane
+    __device__ __forceinline__ void force2(const Lat<float> &L, int cx, int cy, float2 &Fx, float2 &Fy) const
     {
-        const float2 v = sr[cy][cx];
-        return k ? v.y : v.x;
-    }
-    // Eq. (8) + Eq. (9) + rho_k g, as force_at (the same operations per species)
-    __device__ __forceinline__ void force(const Lat<float> &L, int k, int cx, int cy, float &Fx, float &Fy) const
-    {
-        if (k) {
-            Fx = F1x;
-            Fy = F1y;
-            return;
-        }
-        auto at_psi = [&](int dy, int dx) -> Sp<float> {
-            const float2 v = sp[cy + dy][cx + dx];
-            return {v.x, v.y};
-        };
-        auto at_rho = [&](int dy, int dx) -> Sp<float> {
-            const float2 v = sr[cy + dy][cx + dx];
-            return {v.x, v.y};
-        };
-        Sp<float> msx, msy, s3x, s3y;
-        vq25c<Sp<float>>(at_psi, L.cw, p25f, msx, msy);
-        vq9<Sp<float>>(at_rho, s3x, s3y);   // component j: sums over species j's density
-        const float2 psi = sp[cy][cx], rho = sr[cy][cx];
-        vforce<float>(psi.x, rho.x, msx.a, msy.a, s3x.b, s3y.b, L.GAB, L.g[0], L.g[1], Fx, Fy);
-        vforce<float>(psi.y, rho.y, msx.b, msy.b, s3x.a, s3y.a, L.GAB, L.g[0], L.g[1], F1x, F1y);
+        auto at_psi = [&](int dy, int dx) { return sp[cy + dy][cx + dx]; };
+        auto at_rho = [&](int dy, int dx) { return sr[cy + dy][cx + dx]; };
+        float2 msx, msy, s3x, s3y;
+        vq25c<float2>(at_psi, L.cw, p25f, msx, msy);
+        vq9<float2>(at_rho, s3x, s3y);   // lane j: sums over species j's density
+        // each species is pushed by the other's density sum
+        vforce<float2>(sp[cy][cx], sr[cy][cx], msx, msy, vswap(s3x), vswap(s3y), L.GAB, L.g[0], L.g[1], Fx, Fy);
     }
     template <int EX, int EY>
-    __device__ __forceinline__ Sp<float> dest(int cx, int cy) const
+    __device__ __forceinline__ float2 dest(int cx, int cy) const
     {
-        const float2 v = sr[cy + EY][cx + EX];
-        return {v.x, v.y};
-    }
-    template <int EX, int EY>
-    __device__ __forceinline__ float density_step(int k, int cx, int cy) const
-    {
-        if (k) return d1;
-        const float2 a = sr[cy][cx], b = sr[cy + EY][cx + EX];
-        d1 = vsub(a.y, b.y);
-        return vsub(a.x, b.x);
+        return sr[cy + EY][cx + EX];
     }
 };
 
@@ -198,48 +172,49 @@ __device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ la
         reinterpret_cast<uint32_t *>(&sm.L)[i] = reinterpret_cast<const uint32_t *>(&G)[i];
     // staged slot (sx, sy) is box column sx + 2, row sy; the same sums as
     // node_density
-    auto slot_density = [&](int k, int sx, int sy) {
-        float v[9];
+    // both species' densities of the slot, as a pair
+    auto slot_density = [&](int sx, int sy) {
+        float2 v[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) v[i] = pop[((k * 9 + i) * H + sy) * W + sx + 2];
-        return vadd(ref[(k * H + sy) * W + sx + 2], vzeroth<float>(v));
+        for (int i = 0; i < 9; ++i)
+            v[i] = make_float2(pop[(i * H + sy) * W + sx + 2], pop[((9 + i) * H + sy) * W + sx + 2]);
+        return vadd(make_float2(ref[sy * W + sx + 2], ref[(H + sy) * W + sx + 2]), vzeroth<float2>(v));
     };
     constexpr int kRing = 4 * SW + 4 * TYv;
     for (int h = tid; h < kRing; h += TX * TYv) {
         int sx, sy;
         ring_slot<TYv>(h, sx, sy);
         if (slot_outside(G, t, sx, sy)) continue;
-        const float rA = slot_density(0, sx, sy), rB = slot_density(1, sx, sy);
-        sm.sr[sy][sx] = make_float2(rA, rB);
-        sm.sp[sy][sx] = make_float2(psi_of<float>(rA), psi_of<float>(rB));
+        const float2 r = slot_density(sx, sy);
+        sm.sr[sy][sx] = r;
+        sm.sp[sy][sx] = make_float2(psi_of<float>(r.x), psi_of<float>(r.y));
     }
     const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
     const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
     const size_t c = (size_t)y * G.pitch + x;
     // the node's own populations stay in the box: collide_site reads them there
     const float *own = pop + cy * W + cx + 2;
-    float fk[2][9], Rn[2], rn[2];
+    float fk[2][9], Rn[2];
+    float2 v[9];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        float v[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) v[i] = own[(k * 9 + i) * H * W];
-        Rn[k] = ref[(k * H + cy) * W + cx + 2];
-        const float r = vadd(Rn[k], vzeroth<float>(v));
-        G.rho[parity ^ 1][(size_t)k * G.plane + c] = r;
-        rn[k] = r;
-    }
-    sm.sr[cy][cx] = make_float2(rn[0], rn[1]);
-    sm.sp[cy][cx] = make_float2(psi_of<float>(rn[0]), psi_of<float>(rn[1]));
+    for (int i = 0; i < 9; ++i) v[i] = make_float2(own[i * H * W], own[(9 + i) * H * W]);
+    const float2 R2 = make_float2(ref[cy * W + cx + 2], ref[(H + cy) * W + cx + 2]);
+    const float2 rn = vadd(R2, vzeroth<float2>(v));
+    Rn[0] = R2.x;
+    Rn[1] = R2.y;
+    G.rho[parity ^ 1][c] = rn.x;
+    G.rho[parity ^ 1][G.plane + c] = rn.y;
+    sm.sr[cy][cx] = rn;
+    sm.sp[cy][cx] = make_float2(psi_of<float>(rn.x), psi_of<float>(rn.y));
     // the node's force-free moments: threads without a halo slot form them
     // before the barrier (while the others stage the halo), the others after
-    NodeMoments<float> nm;
+    NodeMoments nm;
     const bool early = tid >= kRing;
-    if (early) node_moments<float>(own, H * W, rn, Rn, nm);
+    if (early) node_moments(own, H * W, rn, R2, nm);
     __syncthreads();
-    if (!early) node_moments<float>(own, H * W, rn, Rn, nm);
+    if (!early) node_moments(own, H * W, rn, R2, nm);
     const bool inner = t.y >= 1 && t.y + TX + 1 <= sm.L.nx && t.z >= 1 && t.z + TYv + 1 <= sm.L.ny;
-    const PairStage<SHv> sg{sm.sr, sm.sp, 0.f, 0.f, 0.f};
+    const PairStage<SHv> sg{sm.sr, sm.sp};
     if (inner) collide_site<float, true, true>(sm.L, G.f[parity ^ 1], sg, fk, Rn, x, y, cx, cy, own, H * W, &nm);
     else collide_site<float, false, true>(sm.L, G.f[parity ^ 1], sg, fk, Rn, x, y, cx, cy, own, H * W, &nm);
 }

@@ -1,6 +1,7 @@
 // lb_vops.cuh -- explicit FP32 arithmetic of the offset-population step,
-// written once for a value of one species (float) and of both species
-// (Sp<float>).  Every operation is an intrinsic that rounds once, exactly as
+// written once for a value of one species (float) and of both species (a
+// float2 pair in the paired FP32 instructions).  Every operation is an
+// intrinsic that rounds once, exactly as
 // written, and that the compiler never contracts with another, so every FP32
 // kernel (two-pass, one-pass, persistent, TMA) evaluates Eqs. (1)-(3), (5),
 // (6), (8), (9) with the same roundings, whatever it stages in shared memory
@@ -18,21 +19,20 @@ __device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf
 __device__ __forceinline__ float vsplat(float c, float) { return c; }
 __device__ __forceinline__ float vdiv(float a, float b) { return __fdiv_rn(a, b); }
 
-// a value of each species
-template <class T>
-struct Sp {
-    T a, b;
-};
-template <class T>
-__device__ __forceinline__ Sp<T> vadd(Sp<T> x, Sp<T> y) { return {vadd(x.a, y.a), vadd(x.b, y.b)}; }
-template <class T>
-__device__ __forceinline__ Sp<T> vsub(Sp<T> x, Sp<T> y) { return {vsub(x.a, y.a), vsub(x.b, y.b)}; }
-template <class T>
-__device__ __forceinline__ Sp<T> vmul(Sp<T> x, Sp<T> y) { return {vmul(x.a, y.a), vmul(x.b, y.b)}; }
-template <class T>
-__device__ __forceinline__ Sp<T> vfma(Sp<T> x, Sp<T> y, Sp<T> z) { return {vfma(x.a, y.a, z.a), vfma(x.b, y.b, z.b)}; }
-template <class T>
-__device__ __forceinline__ Sp<T> vsplat(float c, Sp<T>) { return {vsplat(c, T{}), vsplat(c, T{})}; }
+// A value of each species as one (A, B) pair in Blackwell's paired FP32
+// instructions: each lane rounds once, exactly as the scalar intrinsic above,
+// so a step written on pairs gives the same bits as one written per species.
+// The code generator merges a paired multiply into a paired add that consumes
+// it (one FFMA2, whatever the rounding suffix), so nothing here adds a rounded
+// product: such sums are written as one fma.  a - b is b * (-1) + a, exact
+// before its one rounding.
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vsplat(float c, float2) { return make_float2(c, c); }
+// each lane gets the other species' value
+__device__ __forceinline__ float2 vswap(float2 a) { return make_float2(a.y, a.x); }
 
 // a constant times / plus a value
 template <class V>
@@ -138,65 +138,62 @@ template <class V>
 __device__ __forceinline__ V vneg(V x) { return vsub(vsplat(0.f, x), x); }
 
 // The node's terms of the collision shared by its directions: u^eq of
-// Eq. (3) from the half-force momenta m_k (Eq. 6), -1.5 u.u, -u.F_k, and
-// w(|e|^2) rho_k, w(|e|^2) dg_k for the three weight classes (dg_k: the sum
-// of the node's offsets from its rounded density).
-template <class V>
+// Eq. (3) from the half-force momenta m_k (Eq. 6) and -1.5 u.u, shared by the
+// species; per species, as (A, B) pairs, F_k, -u.F_k, and w(|e|^2) rho_k,
+// w(|e|^2) dg_k for the three weight classes (dg_k: the sum of the node's
+// offsets from its rounded density).
 struct OffTerms {
-    V ux, uy, m15uu;
-    V nuF[2];
-    V F[2][2];
-    V wr[2][3], wdg[2][3];
+    float ux, uy, m15uu;
+    float2 Fx, Fy, nuF;
+    float2 wr[3], wdg[3];
 };
 
-template <class V>
-__device__ __forceinline__ void off_terms(float om0, float om1, const V (&rho)[2], const V (&m)[2][2], const V (&F)[2][2],
-                                          const V (&dg)[2], OffTerms<V> &t)
+__device__ __forceinline__ void off_terms(float2 om, float2 rho, float2 mx, float2 my, float2 Fx, float2 Fy, float2 dg,
+                                          OffTerms &t)
 {
-    const V den = cfma(om1, rho[1], cmul(om0, rho[0]));
-    const V nx = cfma(om1, m[1][0], cmul(om0, m[0][0]));
-    const V ny = cfma(om1, m[1][1], cmul(om0, m[0][1]));
+    const float den = vfma(om.y, rho.y, vmul(om.x, rho.x));
+    const float nx = vfma(om.y, mx.y, vmul(om.x, mx.x));
+    const float ny = vfma(om.y, my.y, vmul(om.x, my.x));
     t.ux = vdiv(nx, den);
     t.uy = vdiv(ny, den);
     t.m15uu = cmul(-1.5f, vfma(t.uy, t.uy, vmul(t.ux, t.ux)));
+    t.Fx = Fx;
+    t.Fy = Fy;
+    t.nuF = vneg(vfma(vsplat(t.uy, Fy), Fy, vmul(vsplat(t.ux, Fx), Fx)));
     const float wc[3] = {(float)(4.0 / 9.0), (float)(1.0 / 9.0), (float)(1.0 / 36.0)};
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        t.F[k][0] = F[k][0];
-        t.F[k][1] = F[k][1];
-        t.nuF[k] = vneg(vfma(t.uy, F[k][1], vmul(t.ux, F[k][0])));
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            t.wr[k][c] = cmul(wc[c], rho[k]);
-            t.wdg[k][c] = cmul(wc[c], dg[k]);
-        }
+    for (int c = 0; c < 3; ++c) {
+        t.wr[c] = cmul(wc[c], rho);
+        t.wdg[c] = cmul(wc[c], dg);
     }
 }
 
-// Post-collision offset of direction I of species k from its offset f:
-// f + omega_k (g^eq - f) + C, with g^eq = w rho_k (3 e.u + 4.5 (e.u)^2 -
+// Post-collision offsets of direction I of both species from their offsets
+// f: f + omega_k (g^eq - f) + C, with g^eq = w rho_k (3 e.u + 4.5 (e.u)^2 -
 // 1.5 u.u) + w dg_k (Eq. 2 less w rho_k) and the Guo term of Eq. (5) as
 // C = 3 (1 - omega_k/2) w [(e.F)(1 + 3 e.u) - u.F] (aw3 = 3 (1 - omega_k/2) w),
-// added in the fma that forms its last product.
-template <int I, class V>
-__device__ __forceinline__ V off_collide(const OffTerms<V> &t, int k, float om, float aw3, V f)
+// added in the fma that forms its last product.  The terms in e.u are the
+// species' common ones.
+template <int I>
+__device__ __forceinline__ float2 off_collide(const OffTerms &t, float2 om, float2 aw3, float2 f)
 {
     constexpr int C = I == 0 ? 0 : (I <= 4 ? 1 : 2);
-    V q, X;
+    float q;
+    float2 X;
     if constexpr (I == 0) {
         q = t.m15uu;
-        X = t.nuF[k];
+        X = t.nuF;
     } else {
         constexpr int B = vbase9(I);
         constexpr float s = vsign9(I);
-        const V e = vbase<B>(t.ux, t.uy);                      // e.u = s e
-        q = vfma(cmul(4.5f, e), e, cfma(3.f * s, e, t.m15uu));  // 4.5 (e.u)^2 + 3 e.u - 1.5 u.u
-        const V tt = cfma(3.f, e, vsplat(s, e));               // s (1 + 3 e.u)
-        const V eF = vbase<B>(t.F[k][0], t.F[k][1]);           // e.F = s eF
-        X = vfma(eF, tt, t.nuF[k]);
+        const float e = vbase<B>(t.ux, t.uy);                      // e.u = s e
+        q = vfma(cmul(4.5f, e), e, cfma(3.f * s, e, t.m15uu));      // 4.5 (e.u)^2 + 3 e.u - 1.5 u.u
+        const float tt = cfma(3.f, e, vsplat(s, e));               // s (1 + 3 e.u)
+        const float2 eF = vbase<B>(t.Fx, t.Fy);                    // e.F = s eF
+        X = vfma(eF, vsplat(tt, eF), t.nuF);
     }
-    const V geq = vfma(t.wr[k][C], q, t.wdg[k][C]);
-    return cfma(aw3, X, cfma(om, vsub(geq, f), f));
+    const float2 geq = vfma(t.wr[C], vsplat(q, f), t.wdg[C]);
+    return vfma(aw3, X, vfma(om, vsub(geq, f), f));
 }
 
 }  // namespace lbk
