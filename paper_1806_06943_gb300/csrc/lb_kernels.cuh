@@ -502,15 +502,14 @@ __global__ void __launch_bounds__(TX *TYv, kCollideMinBlocks<real, TYv>)
     collide_tile<real, TYv, false>(lats, tiles[tile_offset + blockIdx.x], parity, sm);
 }
 
-// The NodeMoments of a node whose populations are in a shared-memory box
-// (box[(k * 9 + i) * box_plane]), rho its densities and Rn its references:
-// the same operations, in the same order, as collide_site's own.
-__device__ __forceinline__ void node_moments(const float *__restrict__ box, int box_plane, float2 rho, float2 Rn,
-                                             NodeMoments &nm)
+// The NodeMoments of a node from its offset populations h (both species as
+// pairs), rho its densities and Rn its references: the same operations, in
+// the same order, as collide_site's own.
+__device__ __forceinline__ void node_moments(const float2 (&h)[9], float2 rho, float2 Rn, NodeMoments &nm)
 {
     float2 f[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = make_float2(box[i * box_plane], box[(9 + i) * box_plane]);
+    for (int i = 0; i < 9; ++i) f[i] = h[i];
     vfirst<float2>(f, nm.jx, nm.jy);
     nm.delta = vsub(rho, Rn);
 #pragma unroll

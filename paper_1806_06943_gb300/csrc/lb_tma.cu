@@ -170,9 +170,31 @@ __device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ la
     const int tid = threadIdx.y * TX + threadIdx.x;
     for (int i = tid; i < (int)(sizeof(Lat<float>) / 4); i += TX * TYv)
         reinterpret_cast<uint32_t *>(&sm.L)[i] = reinterpret_cast<const uint32_t *>(&G)[i];
-    // staged slot (sx, sy) is box column sx + 2, row sy; the same sums as
-    // node_density
-    // both species' densities of the slot, as a pair
+    // staged slot (sx, sy) is box column sx + 2, row sy; its densities are
+    // the sums of node_density.  The node's own density and force-free moments from one read of its
+    // populations, then the densities of the halo ring
+    const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
+    const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
+    const size_t c = (size_t)y * G.pitch + x;
+    // the node's own populations stay in the box: collide_site reads them there
+    const float *own = pop + cy * W + cx + 2;
+    float fk[2][9], Rn[2];
+    NodeMoments nm;
+    {
+        float2 v[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) v[i] = make_float2(own[i * H * W], own[(9 + i) * H * W]);
+        const float2 R2 = make_float2(ref[cy * W + cx + 2], ref[(H + cy) * W + cx + 2]);
+        const float2 rn = vadd(R2, vzeroth<float2>(v));
+        Rn[0] = R2.x;
+        Rn[1] = R2.y;
+        G.rho[parity ^ 1][c] = rn.x;
+        G.rho[parity ^ 1][G.plane + c] = rn.y;
+        sm.sr[cy][cx] = rn;
+        sm.sp[cy][cx] = make_float2(psi_of<float>(rn.x), psi_of<float>(rn.y));
+        node_moments(v, rn, R2, nm);
+    }
+    // both species' densities of a ring slot
     auto slot_density = [&](int sx, int sy) {
         float2 v[9];
 #pragma unroll
@@ -189,30 +211,7 @@ __device__ __forceinline__ void fused_tile_box(const Lat<float> *__restrict__ la
         sm.sr[sy][sx] = r;
         sm.sp[sy][sx] = make_float2(psi_of<float>(r.x), psi_of<float>(r.y));
     }
-    const int x = t.y + threadIdx.x, y = t.z + threadIdx.y;
-    const int cx = threadIdx.x + HALO, cy = threadIdx.y + HALO;
-    const size_t c = (size_t)y * G.pitch + x;
-    // the node's own populations stay in the box: collide_site reads them there
-    const float *own = pop + cy * W + cx + 2;
-    float fk[2][9], Rn[2];
-    float2 v[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) v[i] = make_float2(own[i * H * W], own[(9 + i) * H * W]);
-    const float2 R2 = make_float2(ref[cy * W + cx + 2], ref[(H + cy) * W + cx + 2]);
-    const float2 rn = vadd(R2, vzeroth<float2>(v));
-    Rn[0] = R2.x;
-    Rn[1] = R2.y;
-    G.rho[parity ^ 1][c] = rn.x;
-    G.rho[parity ^ 1][G.plane + c] = rn.y;
-    sm.sr[cy][cx] = rn;
-    sm.sp[cy][cx] = make_float2(psi_of<float>(rn.x), psi_of<float>(rn.y));
-    // the node's force-free moments: threads without a halo slot form them
-    // before the barrier (while the others stage the halo), the others after
-    NodeMoments nm;
-    const bool early = tid >= kRing;
-    if (early) node_moments(own, H * W, rn, R2, nm);
     __syncthreads();
-    if (!early) node_moments(own, H * W, rn, R2, nm);
     const bool inner = t.y >= 1 && t.y + TX + 1 <= sm.L.nx && t.z >= 1 && t.z + TYv + 1 <= sm.L.ny;
     const PairStage<SHv> sg{sm.sr, sm.sp};
     if (inner) collide_site<float, true, true>(sm.L, G.f[parity ^ 1], sg, fk, Rn, x, y, cx, cy, own, H * W, &nm);
