@@ -225,7 +225,7 @@ template <int TYv>
 __global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
     k_fused_tma(const Lat<float> *__restrict__ lats, const int4 *__restrict__ tiles, int tile_offset, int parity,
                 const TmaMaps *__restrict__ maps, int *err, long long wait_cycles, int drop_tile, int n_tiles,
-                int ahead)
+                int ahead, int wave)
 {
     using B = TmaBox<TYv>;
     constexpr int ti = TYv == 2 ? 0 : (TYv == 4 ? 1 : 2);
@@ -238,6 +238,18 @@ __global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
         return;
     }
     const int tid = threadIdx.y * TX + threadIdx.x;
+    // the boxes of the tile `ahead` blocks later (about one wave of resident
+    // blocks) into L2, so that its copies find them there; a block of the
+    // first wave issues it once its own box has landed, so that it does not
+    // compete with the first wave's own copies
+    const bool first_wave = (int)blockIdx.x < wave;
+    auto prefetch_ahead = [&]() {
+        if (ahead > 0 && (int)blockIdx.x + ahead < n_tiles) {
+            const int4 tn = tiles[tile_offset + blockIdx.x + ahead];
+            tma_prefetch_3d(&maps[tn.x].pop[ti][parity], tn.y - 4, tn.z - HALO, 0);
+            tma_prefetch_3d(&maps[tn.x].ref[ti][parity], tn.y - 4, tn.z - HALO, 0);
+        }
+    };
     // the copy of drop_tile (a test hook) is never started: its wait runs out
     const bool issued = tile_offset + (int)blockIdx.x != drop_tile;
     if (tid == 0) {
@@ -248,13 +260,7 @@ __global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
             tma_load_3d(box, &maps[t.x].pop[ti][parity], t.y - 4, t.z - HALO, 0, &bar);
             tma_load_3d(box + B::kPop, &maps[t.x].ref[ti][parity], t.y - 4, t.z - HALO, 0, &bar);
         }
-        // the boxes of the tile `ahead` blocks later (about one wave of
-        // resident blocks) into L2, so that its copies find them there
-        if (ahead > 0 && (int)blockIdx.x + ahead < n_tiles) {
-            const int4 tn = tiles[tile_offset + blockIdx.x + ahead];
-            tma_prefetch_3d(&maps[tn.x].pop[ti][parity], tn.y - 4, tn.z - HALO, 0);
-            tma_prefetch_3d(&maps[tn.x].ref[ti][parity], tn.y - 4, tn.z - HALO, 0);
-        }
+        if (!first_wave) prefetch_ahead();
     }
     // halo slots beyond the lattice load their nodes directly (wrapped, or
     // wall ghost rows): done while the copy is in flight
@@ -285,6 +291,7 @@ __global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
         }
         return;
     }
+    if (tid == 0 && first_wave) prefetch_ahead();
     fused_tile_box<TYv>(lats, t, parity, sm, box, box + B::kPop);
 }
 
@@ -314,7 +321,7 @@ struct TmaKernel {
     {
         k_fused_tma<TYv><<<n_tiles, dim3(TX, TYv), kSmem, s>>>(lats, tiles, tile_offset, parity, maps, err, wait_cycles,
                                                                drop_tile, n_tiles,
-                                                               kPrefetchQuarterWaves * grid_wave / 4);
+                                                               kPrefetchQuarterWaves * grid_wave / 4, grid_wave);
         return cudaGetLastError();
     }
 };
