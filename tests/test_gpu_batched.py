@@ -2,9 +2,10 @@
 persistent launch per 64 steps, one-pass steps, or TMA-staged one-pass steps
 in FP32; tile heights 2, 4, 8) gives the same populations bit for bit, in
 FP64 (the plain evaluation order) and in FP32 (every rounding spelled out,
-the same in every kernel); the persistent kernel's bounded waits end with LB_ETIMEOUT when a
-tile never reports; the autotuner leaves the state untouched and caches its
-choice."""
+the same in every kernel); a batch stepped in the two chains of its step
+graph matches its lattices stepped alone; the persistent kernel's bounded
+waits end with LB_ETIMEOUT when a tile never reports; the autotuner leaves
+the state untouched and caches its choice."""
 import numpy as np
 import pytest
 
@@ -69,6 +70,26 @@ def test_all_configurations_agree(lbmod, oracle_mod, precision):
             fo = o.fields()
             den = np.max(np.abs(fo["rho"]))
             assert np.max(np.abs(ref_fields[i]["rho"] - fo["rho"])) <= 1e-12 * den, i
+
+
+@pytest.mark.parametrize("config", [(3, 8), (2, 4), (0, 4)])
+def test_batch_in_two_chains_equals_single_lattices(lbmod, config):
+    """A batch's step graph runs its lattices as two chains on two streams
+    (groups of about equal node counts); every lattice ends with the same
+    populations as the same lattice stepped alone, in one chain, bit for bit
+    (FP32; graph replays plus single steps)."""
+    rhos = fields_for(SPECS)
+    steps = 2 * 32 + 3
+    b = run_batch(lbmod, 1, config, steps, rhos)
+    for i, s in enumerate(SPECS):
+        kw = {k: v for k, v in s.items() if k not in ("nx", "ny")}
+        L = lbmod.Lattice(s["nx"], s["ny"], precision=1, **kw, **C6)
+        L.set_config(*config)
+        L.set_fields(rhos[i])
+        L.step(steps)
+        got, ref = b.fields(i), L.fields()
+        for k in ("rho", "mom"):
+            assert np.array_equal(got[k], ref[k]), (config, i, k)
 
 
 def test_persistent_wait_times_out_and_device_recovers(lbmod):
