@@ -318,7 +318,14 @@ int lb_step_vjp(lb_handle *h, const double *w, double *out, double dtheta[5]);
 /* Create n >= 1 lattices of possibly different sizes and parameters that
  * are stepped together: each time step is one launch of each kernel over the
  * tiles of all lattices.  All p[i].precision must agree; the stream of p[0]
- * is used. */
+ * is used.  With n >= 2, lb_batch_step runs the lattices as two chains
+ * (groups of about equal node counts, each launch over one group's tiles):
+ * the second on a non-blocking stream the batch creates and owns, forked
+ * from and joined back to the batch's stream by events inside each step
+ * call, so work the caller enqueues on that stream afterwards still sees
+ * every lattice stepped.  The populations are the same bit for bit as with
+ * one launch per step.  lb_batch_profile times single launches over all
+ * tiles. */
 int lb_batch_create(const lb_params *p, int32_t n, lb_batch **out);
 void lb_batch_destroy(lb_batch *b);
 int lb_batch_size(const lb_batch *b);
