@@ -427,8 +427,12 @@ struct lb_engine {
         for (int ti = 0; ti < 3; ++ti) {
             const int tyv = kTileHeights[ti];
             std::vector<int4> box, rest;
-            for (const int4 &t : stiles[ti])
-                (lbk::tma_box_tile(P[t.x].nx, P[t.x].ny, t.y, t.z, tyv) ? box : rest).push_back(t);
+            for (const int4 &t : stiles[ti]) {
+                if (lbk::tma_box_tile(P[t.x].nx, P[t.x].ny, t.y, t.z, tyv))
+                    box.push_back(make_int4(t.x, t.y, t.z, lbk::kTmaBoxMark));
+                else
+                    rest.push_back(t);
+            }
             n_box[ti] = (int)box.size();
             box.insert(box.end(), rest.begin(), rest.end());
             if (cudaMalloc((void **)&d_btiles[ti], box.size() * sizeof(int4)) != cudaSuccess) {
@@ -1267,7 +1271,7 @@ int engine_create(const lb_params *p, int n, lb_engine **out)
                 for (int pass = 0; pass < 2; ++pass) {
                     for (const int4 &t : e->stiles[ti])
                         if (group[t.x] == g && lbk::tma_box_tile(p[t.x].nx, p[t.x].ny, t.y, t.z, tyv) == (pass == 0))
-                            list.push_back(t);
+                            list.push_back(make_int4(t.x, t.y, t.z, pass == 0 ? lbk::kTmaBoxMark : 0));
                     if (pass == 0) e->c_box[ti][g] = (int)list.size() - e->c_off[ti][g];
                 }
                 e->c_cnt[ti][g] = (int)list.size() - e->c_off[ti][g];

@@ -65,17 +65,21 @@ __host__ __device__ inline bool tma_box_tile(int nx, int ny, int x0, int y0, int
 {
     return x0 + 32 <= nx && y0 + ty <= ny && nx >= kTmaBoxW && ny >= ty + 4;
 }
+// Fourth field (w) of a tile record that tma_box_tile accepted, set where
+// the host sorts a list into box tiles and the rest (the others keep 0), so
+// that the TMA kernel checks its tile without loading its lattice first.
+constexpr int kTmaBoxMark = 1;
 // Shared-memory opt-in of the TMA kernels on the current device; call once
 // before the first launch_fused_tma, outside stream capture.
 cudaError_t prepare_fused_tma();
 // One time step of the FP32 tiles [tile_offset, tile_offset + n_tiles) in
 // one pass, one block per tile, each tile staged by one TMA copy of its
 // population box and one of its reference-density box.  Every tile must be
-// full and of a lattice at least kTmaBoxW x (ty + 4) nodes (tma_box_tile);
-// the others go to Launch<float>::fused.  A copy not complete after
-// wait_cycles SM clocks sets *err = 1 and ends the block, a tile that is not
-// a box tile sets *err = 2; the copy of tile drop_tile (a test hook, -1 for
-// none) is never started.
+// full and of a lattice at least kTmaBoxW x (ty + 4) nodes (tma_box_tile)
+// and carry w = kTmaBoxMark; the others go to Launch<float>::fused.  A copy
+// not complete after wait_cycles SM clocks sets *err = 1 and ends the block,
+// a tile without the mark sets *err = 2 (and starts no copy); the copy of
+// tile drop_tile (a test hook, -1 for none) is never started.
 cudaError_t launch_fused_tma(const Lat<float> *lats, const int4 *tiles, int tile_offset, int n_tiles, int parity,
                              const TmaMaps *maps, int *err, long long wait_cycles, int drop_tile, int ty, cudaStream_t s);
 

@@ -40,12 +40,6 @@ constexpr int kTmaMinBlocks = (225 * 1024) / (TmaBox<TYv>::kBytes + 8 * 1024) < 
                                   ? (225 * 1024) / (TmaBox<TYv>::kBytes + 8 * 1024)
                                   : kCollideMinBlocks<float, TYv>;
 
-// the tile is full and its lattice holds a whole box (so its maps exist)
-__device__ __forceinline__ bool box_tile(const Lat<float> &G, int4 t, int tyv)
-{
-    return tma_box_tile(G.nx, G.ny, t.y, t.z, tyv);
-}
-
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
@@ -232,11 +226,13 @@ __global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
     extern __shared__ __align__(128) float box[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ PairSmem<TYv> sm;
+    // the tile is full and its lattice holds a whole box (so its maps exist):
+    // the host marked it so when it sorted the list (tma_box_tile), which
+    // keeps the lattice's descriptor off the way to the copy.  A tile without
+    // the mark starts no copy and no load and leaves with *err = 2 where a
+    // failed wait would (block-uniform, no early branch in the prologue)
     const int4 t = tiles[tile_offset + blockIdx.x];
-    if (!box_tile(lats[t.x], t, TYv)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(err, 2);
-        return;
-    }
+    const bool good = t.w == kTmaBoxMark;
     const int tid = threadIdx.y * TX + threadIdx.x;
     // the boxes of the tile `ahead` blocks later (about one wave of resident
     // blocks) into L2, so that its copies find them there; a block of the
@@ -251,7 +247,7 @@ __global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
         }
     };
     // the copy of drop_tile (a test hook) is never started: its wait runs out
-    const bool issued = tile_offset + (int)blockIdx.x != drop_tile;
+    const bool issued = good && tile_offset + (int)blockIdx.x != drop_tile;
     if (tid == 0) {
         mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -260,13 +256,13 @@ __global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
             tma_load_3d(box, &maps[t.x].pop[ti][parity], t.y - 4, t.z - HALO, 0, &bar);
             tma_load_3d(box + B::kPop, &maps[t.x].ref[ti][parity], t.y - 4, t.z - HALO, 0, &bar);
         }
-        if (!first_wave) prefetch_ahead();
+        if (good && !first_wave) prefetch_ahead();
     }
     // halo slots beyond the lattice load their nodes directly (wrapped, or
     // wall ghost rows): done while the copy is in flight
     {
         const Lat<float> &G = lats[t.x];
-        if (t.y == 0 || t.y + TX + HALO > G.nx || t.z < HALO || t.z + TYv + HALO > G.ny) {
+        if (good && (t.y == 0 || t.y + TX + HALO > G.nx || t.z < HALO || t.z + TYv + HALO > G.ny)) {
             constexpr int kRing = 4 * SW + 4 * TYv;
             for (int h = tid; h < kRing; h += TX * TYv) {
                 int sx, sy;
@@ -281,10 +277,10 @@ __global__ void __launch_bounds__(TX *TYv, kTmaMinBlocks<TYv>)
         }
     }
     __syncthreads();   // the barrier is initialised before anyone waits on it
-    const bool ok = mbar_wait(&bar, 0, wait_cycles);
+    const bool ok = good && mbar_wait(&bar, 0, wait_cycles);
     if (!__syncthreads_and(ok)) {
         if (tid == 0) {
-            atomicExch(err, 1);
+            atomicExch(err, good ? 1 : 2);
             // let a copy still in flight land before the block ends (bounded
             // too, by at least 2^31 clocks, ~1 s)
             if (issued) mbar_wait(&bar, 0, wait_cycles > (1ll << 31) ? wait_cycles : (1ll << 31));
